@@ -1,0 +1,118 @@
+"""Plant plausible mistakes in a copy of the oracle and check that its pins catch each.
+
+Every mutant is one textual change to ``oracle/oracle.c`` (a dropped term, a wrong
+sign, coefficient, index or operand), compiled into a throw-away library and run
+against the pin battery below in a child process. A mutant that passes every pin
+would mean the pins leave that part of the oracle unchecked.
+"""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "oracle.c")
+
+MUTANTS = [
+    ("feq quadratic coefficient", "+ 4.5 * cu * cu - 1.5 * uu);\n}", "+ 4.0 * cu * cu - 1.5 * uu);\n}"),
+    ("feq u^2 sign", "4.5 * cu * cu - 1.5 * uu);\n}", "4.5 * cu * cu + 1.5 * uu);\n}"),
+    ("feq linear coefficient", "(1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);\n}", "(1.0 + 2.0 * cu + 4.5 * cu * cu - 1.5 * uu);\n}"),
+    ("Guo prefactor", "return (1.0 - 0.5 / tau) * W[i]", "return (1.0 - 1.0 / tau) * W[i]"),
+    ("Guo u.F sign", "3.0 * (cF - uF) + 9.0 * cu * cF);\n}", "3.0 * (cF + uF) + 9.0 * cu * cF);\n}"),
+    ("Guo second-order term dropped", "3.0 * (cF - uF) + 9.0 * cu * cF);\n}", "3.0 * (cF - uF) + 0.0 * cu * cF);\n}"),
+    ("half-force velocity shift dropped",
+     "u[a] = (j[a] + 0.5 * F[a]) / rho;\n    if (type == INLET)", "u[a] = (j[a] + 0.0 * F[a]) / rho;\n    if (type == INLET)"),
+    ("BGK relaxation time", "out[i] = f[i] - (f[i] - feq(i, rho, u)) / tau + guo", "out[i] = f[i] - (f[i] - feq(i, rho, u)) / (tau + 0.1) + guo"),
+    ("inlet density", "out[i] = feq(i, rho, u_in);", "out[i] = feq(i, 1.0, u_in);"),
+    ("outlet density", "out[i] = feq(i, rho_out, u);", "out[i] = feq(i, rho, u);"),
+    ("bounce-back takes own direction",
+     "f[i] = A[opp(i) * N + n];\n                }\n                force_at", "f[i] = A[i * N + n];\n                }\n                force_at"),
+    ("push instead of pull", "int p[3] = {x - C[i][0], y - C[i][1], z - C[i][2]};", "int p[3] = {x + C[i][0], y + C[i][1], z + C[i][2]};"),
+    ("periodic wrap off by one", "p[a] = (p[a] + n[a]) % n[a];", "p[a] = (p[a] + n[a] + 1) % n[a];"),
+    ("gather from solid nodes",
+     "if (source_node(x, y, z, i, nx, ny, nz, periodic, &s) && nt[s] != SOLID)\n                        f[i] = A[i * N + s];",
+     "if (source_node(x, y, z, i, nx, ny, nz, periodic, &s))\n                        f[i] = A[i * N + s];"),
+    ("diagonal weight", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 35.0};"),
+    ("velocity table", "{0, -1, 1}, {0, -1, -1}};", "{0, -1, 1}, {0, 1, -1}};"),
+    ("reported velocity shift sign", "u[a * N + n] = (j[a] - 0.5 * F[a]) / r;", "u[a * N + n] = (j[a] + 0.5 * F[a]) / r;"),
+    ("reduced momentum shift sign", "p[a] += j[a] - 0.5 * F[a];", "p[a] += j[a] + 0.5 * F[a];"),
+    ("tiling drops boundary-only tiles", "if (nt[x + (long)nx * (y + (long)ny * z)] != SOLID) keep = 1;",
+     "if (nt[x + (long)nx * (y + (long)ny * z)] == FLUID) keep = 1;"),
+    ("tiling index order", "long t = tx + (long)Tx * (ty + (long)Ty * tz);\n                int keep",
+     "long t = ty + (long)Ty * (tx + (long)Tx * tz);\n                int keep"),
+    ("tiled slot transposed", "src_s = (sx & 3) + 4 * (sy & 3) + 16 * (sz & 3);", "src_s = (sy & 3) + 4 * (sx & 3) + 16 * (sz & 3);"),
+    ("adjoint: relaxation factor dropped", "mu[i] += lam[i] * (1.0 - 1.0 / tau);", "mu[i] += lam[i];"),
+    ("adjoint: half-force term", "Fbar[a] += 0.5 * ubar[a] / rho;", "Fbar[a] += ubar[a] / rho;"),
+    ("adjoint: bounce-back transpose", "lam[opp(i) * N + n] += mu[i];", "lam[i * N + n] += mu[i];"),
+    ("adjoint: Guo prefactor derivative", "lam[i] * W[i] * qi * 0.5 / (tau * tau);", "lam[i] * W[i] * qi * 0.5 / tau;"),
+    ("loss seed sign", "lam[i * N + n] = (C[i][0] - ux) / r / (double)count;", "lam[i * N + n] = (C[i][0] + ux) / r / (double)count;"),
+    ("tangent quotient rule", "(a.d * b.v - a.v * b.d) / (b.v * b.v)", "(a.d * b.v + a.v * b.d) / (b.v * b.v)"),
+]
+
+
+def _battery():
+    """Pins in order of cost; returns the name of the first that fails, or None."""
+    import test_oracle_adjoint as A
+    import test_oracle_pins as P
+    checks = [
+        ("lattice constants", P.test_lattice_matches_paper_constants),
+        ("lattice isotropy", P.test_lattice_isotropy),
+        ("collision moments", lambda: [P.test_collision_moments_fluid(s) for s in range(2)]),
+        ("single relaxation", lambda: P.test_collision_single_relaxation_rate(0)),
+        ("boundary closures", P.test_collision_boundary_closures),
+        ("tiling golden", P.test_tiling_channel8_golden),
+        ("tiling brute force", lambda: [P.test_tiling_brute_force(s) for s in range(4)]),
+        ("equilibrium fixed point", P.test_equilibrium_fixed_point_with_walls),
+        ("uniform flow fixed point", P.test_uniform_flow_fixed_point_periodic),
+        ("mass", lambda: P.test_mass_conservation(1e-4)),
+        ("momentum closed form", P.test_momentum_closed_form),
+        ("uniform acceleration", P.test_uniform_acceleration_closed_form),
+        ("streaming shift", P.test_streaming_is_shift_when_collision_off),
+        ("time reversal", P.test_streaming_time_reversal_with_walls),
+        ("dense vs tiled", lambda: [P.test_dense_and_tiled_bit_identical(p) for p in (0, 7, 5)]),
+        ("tangent vs FD", lambda: A.test_tangent_matches_central_differences(0b111)),
+        ("dot product", lambda: [A.test_adjoint_dot_product(p) for p in (0, 7)]),
+        ("loss gradient", lambda: A.test_loss_gradient_matches_fd(True)),
+        ("shear wave", P.test_shear_wave_decay_rate),
+        ("Poiseuille", P.test_poiseuille_closed_form),
+    ]
+    for name, fn in checks:
+        try:
+            fn()
+        except Exception:
+            return name
+    return None
+
+
+def _compile(text, out):
+    with open(out + ".c", "w") as fh:
+        fh.write(text)
+    subprocess.run(["gcc", "-O2", "-ffp-contract=off", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+                    "-w", out + ".c", "-o", out, "-lm"], check=True)
+
+
+def test_every_mutant_is_caught():
+    src = open(SRC).read()
+    survivors = []
+    with tempfile.TemporaryDirectory() as td:
+        for k, (name, old, new) in enumerate(MUTANTS):
+            assert src.count(old) == 1, f"mutation site not unique: {name}"
+            so = os.path.join(td, f"m{k}.so")
+            _compile(src.replace(old, new), so)
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), so], cwd=ROOT,
+                               capture_output=True, text=True, timeout=300)
+            caught = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else f"exit {r.returncode}"
+            if r.returncode == 0 and caught == "SURVIVED":
+                survivors.append(name)
+    assert not survivors, f"mutants not caught by any pin: {survivors}"
+
+
+if __name__ == "__main__":
+    sys.path.insert(0, ROOT)
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from oracle import oracle as O
+    O._lib = O.load(sys.argv[1])
+    failed = _battery()
+    print("SURVIVED" if failed is None else f"CAUGHT by {failed}")
