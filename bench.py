@@ -1,0 +1,310 @@
+#!/usr/bin/env python
+"""Benchmark of the fused D3Q19 BGK sparse-tile step on GB300.
+
+Workload (default): periodic sphere-pack porous medium, 256^3 nodes, overlapping
+solid spheres of radius 8 with uniform seeded centres (seed 161102445) until the
+porosity first reaches 0.35; D3Q19 BGK with tau = 0.7, body force g_x = 1e-5 (Guo),
+periodic faces, 4^3 tiles with all-solid tiles skipped; FP64 storage. A step is one
+fused collide-and-stream launch over all kept tiles; the metric is MFLUPS, 10^6
+non-solid node updates per second (Sec. 4.1 of the paper).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--dtype f64|f32|f16s]
+  python bench.py --impl reference ...     # the FP64 CPU oracle on the host cores
+
+Under torchrun every rank runs its own replica of the workload (the path has no data
+exchange between replicas); value = all ranks' node updates / the slowest rank's time.
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MFLUPS (10^6 non-solid node updates per second) of the fused D3Q19 BGK sparse-tile step"
+WORKLOAD = ("porous sphere pack 256^3, radius 8, porosity 0.35, seed 161102445, D3Q19 BGK, "
+            "tau 0.7, g_x 1e-5 (Guo), periodic, 4^3 tiles, all-solid tiles skipped")
+BYTES_PER_VALUE = {"f64": 8, "f32": 4, "f16s": 2}
+DTYPE_NAME = {"f64": "f64", "f32": "f32", "f16s": "f16 (f - w shifted storage), f32 arithmetic"}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples taken while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"lbm_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=self.fh,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_baseline(nt, steps_hint: int, budget_s: float, tau, g):
+    """Time the FP64 oracle (as it stands) on the host cores on the full geometry."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    f = O.init(nt)
+    B = f.copy()
+    n = int(np.count_nonzero(nt))
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps_hint and (time.perf_counter() - t0) < budget_s:
+        O.step(f, nt, 0b111, tau, g, nthreads=threads, out=B)
+        f, B = B, f
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * done / dt / 1e6, "unit": "MFLUPS", "cores": threads, "kind": "oracle",
+            "sample": f"{done} full steps of the 256^3 porous workload ({n} non-solid nodes), "
+                      f"dense FP64 oracle, OpenMP over z on {threads} threads, {dt:.1f} s"}
+
+
+def run_reference(args, nt, tau, g):
+    """--impl reference: the oracle on the host cores; each step is one oracle step on a
+    z-slab sample of the workload, sized so the whole run ends in about two minutes."""
+    from oracle import oracle as O
+    threads = os.cpu_count() or 1
+    total = args.steps + args.warmup
+
+    def slab(nz_s):
+        s = np.ascontiguousarray(nt[:nz_s])
+        return s, O.init(s)
+
+    probe, fp = slab(16)
+    Bp = fp.copy()
+    t = time.perf_counter()
+    O.step(fp, probe, 0b011, tau, g, nthreads=threads, out=Bp)
+    t16 = max(time.perf_counter() - t, 1e-4)
+    nz_s = int(max(4, min(256, 16 * (120.0 / total) / t16)) // 4 * 4)
+    s, f = slab(nz_s)
+    B = f.copy()
+    n = int(np.count_nonzero(s))
+    for _ in range(args.warmup):
+        O.step(f, s, 0b011, tau, g, nthreads=threads, out=B)
+        f, B = B, f
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        O.step(f, s, 0b011, tau, g, nthreads=threads, out=B)
+        f, B = B, f
+    dt = time.perf_counter() - t0
+    value = n * args.steps / dt / 1e6
+    sample = (f"z-slab 256x256x{nz_s} of the workload ({n} non-solid nodes; x, y periodic, z walls), "
+              f"one dense FP64 oracle step per benchmark step, OpenMP over z on {threads} threads")
+    return {"metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "MFLUPS", "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "MFLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16s"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    from paper_1611_02445_gb300 import inputs as I
+    tau, g = 0.7, (1e-5, 0.0, 0.0)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        nt = I.sphere_pack(256, 8.0, 0.35, I.SEED_POROUS_256)
+        print(json.dumps(run_reference(args, nt, tau, g)), flush=True)
+        return
+
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__
+    from paper_1611_02445_gb300 import lbm
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    __graft_entry__.build()
+    nt = I.sphere_pack(256, 8.0, 0.35, I.SEED_POROUS_256)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+
+    L = lbm.Lattice(nt, args.dtype, 0b111, stream)
+    info = L.info()
+    L.set_params(tau, g)
+    L.init_equilibrium()
+    n_nonsolid = info["n_nonsolid"]
+    L.step(args.warmup)
+    torch.cuda.synchronize()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(local_rank)
+    barrier()
+    sampler.start()
+    time.sleep(0.3)
+    ev0.record(stream)
+    L.step(args.steps)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    barrier()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    mass, _ = L.reduce()
+    assert np.isfinite(mass)
+    value = n_nonsolid * args.steps * world / (ms_max * 1e-3) / 1e6
+
+    # roofline of the step kernel: algorithmic bytes B_node = 2 * 19 * n_d per non-solid
+    # node update (Eq. 10) over the average launch duration
+    nd = BYTES_PER_VALUE[args.dtype]
+    launch_s = ms / args.steps * 1e-3
+    alg_bytes = n_nonsolid * 2 * 19 * nd
+    peaks, peak_src = load_peaks()
+    hbm_peak = float(peaks["hbm_gbs"])
+    achieved_gbs = alg_bytes / launch_s / 1e9
+    roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved_gbs / hbm_peak, "traffic": None,
+            "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
+            "algorithmic_bytes_per_launch": alg_bytes}
+    if args.dtype == "f64":
+        # FP64 arithmetic bounds this kernel on GB300: FP64 FLOPs executed per non-solid
+        # node update, counted with ncu (2 * dfma + dadd + dmul per node), over the FP64
+        # peak of 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz.
+        flops_per_node = FP64_FLOPS_PER_NODE
+        fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
+        achieved_tf = n_nonsolid * flops_per_node / launch_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved_tf / fp64_peak, "traffic": None,
+                "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (probe measured 1.20)",
+                "fp64_flops_per_node_update": flops_per_node,
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak}}
+
+    line = {"metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": WORKLOAD, "storage": DTYPE_NAME[args.dtype], "n_nonsolid": n_nonsolid,
+                       "n_tiles": info["n_tiles"], "eta_t": info["eta_t"],
+                       "state_bytes": 2 * info["copy_bytes"],
+                       "l2_policy": "inputs larger than L2 (two population copies of "
+                                    f"{info['copy_bytes'] / 1e9:.2f} GB each vs 126 MB L2)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": roof, "gpu_launches": args.steps, "clocks": clocks}
+
+    # end to end through the public API: host node types in, host results out
+    if not args.no_e2e:
+        L.close()
+        pinned_nt = torch.from_numpy(nt.reshape(-1)).pin_memory()
+        nz, ny, nx = nt.shape
+        rho_h = torch.empty((nz, ny, nx), dtype=torch.float32).pin_memory()
+        u_h = torch.empty((3, nz, ny, nx), dtype=torch.float32).pin_memory()
+        barrier()
+        t0 = time.perf_counter()
+        ctx = lbm.lbm_create(pinned_nt.numpy(), nx, ny, nz, 4, lbm.DTYPES[args.dtype], 0b111, stream)
+        lbm.lbm_set_params(ctx, tau, g)
+        lbm.lbm_init_equilibrium(ctx)
+        lbm.lbm_step(ctx, args.steps)
+        mass_e2e, _ = lbm.lbm_reduce(ctx)
+        lbm.lbm_macroscopic(ctx, rho_h.numpy(), u_h.numpy(), out_f64=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        lbm.lbm_destroy(ctx)
+        te = torch.tensor([dt], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        dt = float(te.item())
+        d2h = 4 * 8 + rho_h.numel() * 4 + u_h.numel() * 4
+        line["e2e"] = {"value": n_nonsolid * args.steps * world / dt / 1e6, "unit": "MFLUPS",
+                       "h2d_bytes_per_step": nt.size / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+                       "includes": "lbm_create from pinned host node types (tile map on GPU), init, "
+                                   f"{args.steps} steps, FP64 reduction and FP32 rho/u export to pinned host"}
+    else:
+        L.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = oracle_baseline(nt, 10, 12.0, tau, g)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# Executed FP64 FLOPs per fluid-node update of the FP64 step kernel (2 dfma + dadd + dmul,
+# from an ncu count divided by the non-solid nodes of the launch).
+FP64_FLOPS_PER_NODE = 340
+
+if __name__ == "__main__":
+    main()

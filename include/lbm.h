@@ -1,0 +1,148 @@
+/*
+ * lbm.h -- C ABI of the GB300 (sm_103a) sparse-tile D3Q19 lattice-Boltzmann library.
+ *
+ * The library implements the fused collide-and-stream time step of Tomczak & Szafran,
+ * "A new GPU implementation for lattice-Boltzmann simulations on sparse geometries":
+ * the geometry is covered by a uniform grid of 4x4x4 tiles, tiles holding only solid
+ * nodes are dropped (Sec. 3.1, Algorithm 1), and one kernel launch performs gather
+ * (pull) streaming, boundary handling, LBGK collision and the store of all 19
+ * populations for every non-solid node (Sec. 3.4, Algorithm 2; Eq. 7).
+ *
+ * Conventions shared by every entry point
+ *   - Status: every call returns an lbm_status; no C++ exception crosses the ABI.
+ *     Errors after which the device state is undefined (LBM_ECUDA, LBM_ENOMEM,
+ *     LBM_EINTERNAL) are sticky: later calls on the context return the same status
+ *     until lbm_destroy. Argument and ordering errors (LBM_EINVAL, LBM_EUNSUPPORTED,
+ *     LBM_ESTATE) change nothing. lbm_last_error() gives a message.
+ *   - Dense arrays are indexed n = x + nx*(y + ny*z) (x fastest, the row order of
+ *     Sec. 3.2). Population arrays are [19][nz][ny][nx]; velocity arrays [3][nz][ny][nx].
+ *   - Direction numbering: 0 rest; 1 E(+x) 2 N(+y) 3 W(-x) 4 S(-y) 5 T(+z) 6 B(-z);
+ *     7 NE 8 NW 9 SW 10 SE; 11 ET 12 EB 13 WT 14 WB; 15 NT 16 NB 17 ST 18 SB
+ *     (e_3 = W = (-1,0,0) as in the paper's Fig. 1; the rest of Fig. 1 is not legible).
+ *   - Node types (one byte per node, the paper's allNodeType of Sec. 3.1): 0 solid,
+ *     1 fluid, 2 velocity inlet, 3 constant-pressure outlet (boundary kinds of Sec. 2.2).
+ *   - Ownership: the context owns every device buffer it allocates (populations,
+ *     tile structures, checkpoints). The caller owns every pointer it passes; the
+ *     library reads or writes them only during the call (device pointers on the
+ *     context's stream, host pointers synchronously).
+ *   - Streams: all device work is queued on the stream given to lbm_create (or
+ *     lbm_set_stream); calls that return host results synchronise that stream.
+ *   - Thread safety: a context must not be used from two threads at once.
+ */
+#ifndef LBM_GB300_H
+#define LBM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+    LBM_OK = 0,
+    LBM_EINVAL = 1,        /* invalid argument (sizes, tau <= 1/2, NaN parameters, ...) */
+    LBM_ENOMEM = 2,        /* device or host allocation failed; nothing leaked */
+    LBM_ECUDA = 3,         /* a CUDA runtime call failed */
+    LBM_EUNSUPPORTED = 4,  /* valid but not implemented (tile size other than 4, ...) */
+    LBM_ESTATE = 5,        /* call out of order, or a state blob that does not match */
+    LBM_ENONFINITE = 6,    /* the mass reduction found NaN or Inf in the state */
+    LBM_ETIMEOUT = 7,      /* reserved: a bounded device-side wait gave up */
+    LBM_EINTERNAL = 8      /* internal consistency check failed */
+} lbm_status;
+
+/* Storage of the populations. Arithmetic is FP64 for LBM_F64 and FP32 otherwise;
+ * LBM_F16S stores h_i = (f_i - w_i) * 2^12 as IEEE binary16 (round to nearest even). */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2 } lbm_dtype;
+
+enum { LBM_SOLID = 0, LBM_FLUID = 1, LBM_INLET = 2, LBM_OUTLET = 3 };
+enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
+
+/* Build a context for one geometry: validate the node types, build the tile map on
+ * the GPU (Algorithm 1 of Sec. 3.1: tile_flag -> exclusive scan in z-y-x tile order ->
+ * scatter of tileMap and nonEmptyTiles), build per-tile neighbour tables and node
+ * masks, and allocate the two population copies A and B (Sec. 3.1, "two copies").
+ *   node_type   nx*ny*nz bytes, dense; host memory if on_device == 0, else a device
+ *               pointer. Values other than 0..3 give LBM_EINVAL.
+ *   tile        must be 4 (the paper's a = 4), else LBM_EUNSUPPORTED.
+ *   periodic    mask of LBM_PERIODIC_*; a periodic axis must be a multiple of 4
+ *               (LBM_EINVAL). A non-periodic axis that is not a multiple of 4 is
+ *               padded with solid nodes (Sec. 3.1).
+ *   stream      cudaStream_t to queue work on (NULL = legacy default stream).
+ *   out         receives the new context, or NULL on failure.
+ * The populations are not initialised: call lbm_init_equilibrium or lbm_set_f. */
+lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, int nz, int tile,
+                      lbm_dtype dtype, unsigned periodic, void* stream, lbm_ctx** out);
+
+/* Release every device buffer of the context. NULL is ignored. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last error of ctx ("" if none); with ctx == NULL, the last error of a
+ * failed lbm_create in this thread. The string lives until the next call on ctx. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Change the stream later work is queued on. */
+lbm_status lbm_set_stream(lbm_ctx* ctx, void* stream);
+
+/* Relaxation time and boundary data (Eq. 2, Eq. 7; Sec. 2.2 boundary conditions).
+ *   tau       LBGK relaxation time, must be > 1/2 and finite (else LBM_EINVAL).
+ *   g         uniform body-force density (Guo forcing), 3 doubles; NULL = zero.
+ *   g_field   optional per-node x component of the force density, nx*ny*nz doubles,
+ *             dense; it replaces g[0] at every node. Host memory if
+ *             g_field_on_device == 0, else a device pointer. NULL removes a field
+ *             set earlier. The library keeps its own tile-major copy.
+ *   u_in      velocity imposed at inlet nodes (3 doubles; NULL = zero).
+ *   rho_out   density imposed at outlet nodes (> 0). */
+lbm_status lbm_set_params(lbm_ctx* ctx, double tau, const double* g, const double* g_field,
+                          int g_field_on_device, const double* u_in, double rho_out);
+
+/* Set both population copies to the equilibrium f^eq(rho0, u0) of Eq. 3 at every
+ * non-solid node. */
+lbm_status lbm_init_equilibrium(lbm_ctx* ctx, double rho0, const double* u0);
+
+/* Advance n >= 0 time steps: n launches of the fused step kernel, each reading the
+ * current copy and writing the other, then swapping them (Sec. 3.1). */
+lbm_status lbm_step(lbm_ctx* ctx, int n);
+
+/* Density and velocity from the stored post-collision populations f*:
+ * rho = sum_i f*_i, u = (sum_i c_i f*_i - F/2) / rho (Eq. 5 with the half-force shift of
+ * Guo forcing); 0 at solid nodes. rho: nx*ny*nz values, u: 3*nx*ny*nz values, dense,
+ * double if out_f64 else float; device pointers if on_device, else host. */
+lbm_status lbm_macroscopic(lbm_ctx* ctx, void* rho, void* u, int out_f64, int on_device);
+
+/* Global invariants over non-solid nodes, accumulated in FP64 with warp shuffles and a
+ * fixed-order second pass (deterministic): *mass = sum f*, momentum = sum (sum c f* - F/2).
+ * Host outputs. Returns LBM_ENONFINITE if the mass is NaN or Inf. */
+lbm_status lbm_reduce(lbm_ctx* ctx, double* mass, double* momentum);
+
+/* Export the populations of the box [x0, x0+bx) x [y0, y0+by) x [z0, z0+bz) as FP64
+ * [19][bz][by][bx] into host memory `out` (for FP16S, f = w + h). Coordinates wrap on
+ * periodic axes; nodes that are solid, padding or outside the domain read NaN. */
+lbm_status lbm_get_f_box(lbm_ctx* ctx, int x0, int y0, int z0, int bx, int by, int bz, double* out);
+
+/* Whole-domain export / import of the current populations, dense FP64
+ * [19][nz][ny][nx] host arrays; solid entries are ignored on import and NaN on export. */
+lbm_status lbm_get_f(lbm_ctx* ctx, double* f_dense);
+lbm_status lbm_set_f(lbm_ctx* ctx, const double* f_dense);
+
+/* Tile structures (Sec. 3.1): tile_map has ceil(nx/4)*ceil(ny/4)*ceil(nz/4) int32 entries
+ * (rank of the tile among the kept tiles, or -1), non_empty has *n_tiles uint32 linear tile
+ * indices t = tx + Tx (ty + Ty tz) in discovery order. Either array may be NULL. Host. */
+lbm_status lbm_get_tiles(lbm_ctx* ctx, int32_t* tile_map, uint32_t* non_empty, int64_t* n_tiles);
+
+/* Sizes: n_tiles kept, n_nonsolid nodes, bytes of one population copy. Any may be NULL. */
+lbm_status lbm_get_info(lbm_ctx* ctx, int64_t* n_tiles, int64_t* n_nonsolid, int64_t* copy_bytes);
+
+/* Copy the current state (populations and step parity) to a host blob, or back.
+ * lbm_save_state with blob == NULL stores the size in *nbytes. The blob carries a
+ * checksum and a hash of the geometry; loading a blob of another geometry, dtype or
+ * with a bad checksum gives LBM_ESTATE. */
+lbm_status lbm_save_state(lbm_ctx* ctx, void* blob, size_t* nbytes);
+lbm_status lbm_load_state(lbm_ctx* ctx, const void* blob, size_t nbytes);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LBM_GB300_H */

@@ -1,0 +1,483 @@
+// lbm_capi.cu -- the extern "C" entry points of liblbm_gb300 (declared in include/lbm.h).
+//
+// Host-side orchestration only: argument validation, device allocation, the order of
+// kernel launches on the context's stream, and host <-> device copies. Every step of
+// the computation runs in the kernels of lbm_tiles.cu and lbm_step.cu.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lbm_internal.cuh"
+
+namespace lbm {
+int reduce_blocks(int64_t n_tiles);
+}
+
+namespace {
+
+thread_local std::string g_create_err;
+
+// Errors that can leave device state undefined poison the context (sticky); argument
+// and ordering errors are reported and leave the context as it was.
+bool is_sticky(lbm_status st) { return st == LBM_ECUDA || st == LBM_ENOMEM || st == LBM_EINTERNAL; }
+
+lbm_status fail(lbm_ctx* c, lbm_status st, const std::string& msg) {
+    if (!c) {
+        g_create_err = msg;
+        return st;
+    }
+    if (c->sticky != LBM_OK) return c->sticky;
+    c->err = msg;
+    if (is_sticky(st)) c->sticky = st;
+    return st;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, const char* what, cudaError_t e) {
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_ENOMEM : LBM_ECUDA,
+                std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(c, call)                                         \
+    do {                                                          \
+        cudaError_t _e = (call);                                  \
+        if (_e != cudaSuccess) return cuda_fail((c), #call, _e);  \
+    } while (0)
+
+#define LBM_CHECK_CTX(c)                                          \
+    do {                                                          \
+        if (!(c)) return LBM_EINVAL;                              \
+        if ((c)->sticky != LBM_OK) return (c)->sticky;            \
+    } while (0)
+
+bool finite3(const double* v) { return !v || (std::isfinite(v[0]) && std::isfinite(v[1]) && std::isfinite(v[2])); }
+
+template <typename T>
+cudaError_t dev_alloc(T** p, size_t count) {
+    *p = nullptr;
+    if (count == 0) count = 1;
+    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+void free_all(lbm_ctx* c) {
+    void* bufs[] = {c->tile_map, c->non_empty, c->nbr, c->smask, c->tflags, c->ntype,
+                    c->f[0],     c->f[1],      c->gfield, c->partials, c->d_out};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    c->tile_map = nullptr;
+    c->non_empty = nullptr;
+    c->nbr = nullptr;
+    c->smask = nullptr;
+    c->tflags = nullptr;
+    c->ntype = nullptr;
+    c->f[0] = c->f[1] = nullptr;
+    c->gfield = nullptr;
+    c->partials = nullptr;
+    c->d_out = nullptr;
+}
+
+// Device-side check that every neighbour entry is -1 or a valid rank.
+__global__ void k_check_nbr(const int32_t* __restrict__ nbr, int64_t n, int64_t n_tiles, int* __restrict__ bad) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = nbr[i];
+        if (v < -1 || v >= n_tiles) atomicOr(bad, 1);
+    }
+}
+
+uint64_t fnv1a(const void* data, size_t n, uint64_t h = 1469598103934665603ull) {
+    const unsigned char* p = static_cast<const unsigned char*>(data);
+    for (size_t i = 0; i < n; i++) {
+        h ^= p[i];
+        h *= 1099511628211ull;
+    }
+    return h;
+}
+
+struct StateHeader {
+    char magic[8];
+    uint32_t version;
+    int32_t dtype;
+    int32_t nx, ny, nz;
+    uint32_t periodic;
+    int64_t n_tiles;
+    uint64_t geometry_hash;
+    uint64_t payload_bytes;
+    uint64_t payload_hash;
+};
+
+lbm_status geometry_hash(lbm_ctx* c, uint64_t* out) {
+    std::vector<uint8_t> nt((size_t)c->n_tiles * lbm::SLOTS);
+    if (c->n_tiles > 0) {
+        LBM_CUDA(c, cudaMemcpyAsync(nt.data(), c->ntype, nt.size(), cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    int32_t dims[4] = {c->nx, c->ny, c->nz, (int32_t)c->periodic};
+    *out = fnv1a(nt.data(), nt.size(), fnv1a(dims, sizeof(dims)));
+    return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_last_error(const lbm_ctx* ctx) { return ctx ? ctx->err.c_str() : g_create_err.c_str(); }
+
+void lbm_destroy(lbm_ctx* ctx) {
+    if (!ctx) return;
+    free_all(ctx);
+    delete ctx;
+}
+
+lbm_status lbm_set_stream(lbm_ctx* ctx, void* stream) {
+    LBM_CHECK_CTX(ctx);
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    return LBM_OK;
+}
+
+lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, int nz, int tile,
+                      lbm_dtype dtype, unsigned periodic, void* stream, lbm_ctx** out) {
+    g_create_err.clear();
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!node_type) return fail(nullptr, LBM_EINVAL, "node_type is NULL");
+    if (tile != lbm::TILE) return fail(nullptr, LBM_EUNSUPPORTED, "only 4x4x4 tiles are supported");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "dimensions must be >= 1");
+    if (dtype != LBM_F64 && dtype != LBM_F32 && dtype != LBM_F16S) return fail(nullptr, LBM_EINVAL, "unknown dtype");
+    if (periodic & ~7u) return fail(nullptr, LBM_EINVAL, "periodic mask has bits other than x, y, z");
+    const int dims[3] = {nx, ny, nz};
+    for (int a = 0; a < 3; a++)
+        if ((periodic & (1u << a)) && dims[a] % lbm::TILE != 0)
+            return fail(nullptr, LBM_EINVAL, "a periodic axis must be a multiple of 4");
+    const int64_t Tx = (nx + 3) / 4, Ty = (ny + 3) / 4, Tz = (nz + 3) / 4;
+    const int64_t nT = Tx * Ty * Tz;
+    if (nT > 0x7fffffffll) return fail(nullptr, LBM_EINVAL, "tile grid larger than 2^31 tiles");
+
+    lbm_ctx* c = new (std::nothrow) lbm_ctx();
+    if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation of the context failed");
+    c->nx = nx; c->ny = ny; c->nz = nz;
+    c->Tx = (int)Tx; c->Ty = (int)Ty; c->Tz = (int)Tz;
+    c->periodic = periodic;
+    c->dtype = dtype;
+    c->stream = static_cast<cudaStream_t>(stream);
+
+    uint8_t* d_nt = nullptr;
+    uint8_t* d_flag = nullptr;
+    int64_t* d_sums = nullptr;
+    int64_t* d_count = nullptr;
+    int* d_bad = nullptr;
+    auto cleanup = [&]() {
+        if (!on_device && d_nt) cudaFree(d_nt);
+        if (d_flag) cudaFree(d_flag);
+        if (d_sums) cudaFree(d_sums);
+        if (d_count) cudaFree(d_count);
+        if (d_bad) cudaFree(d_bad);
+    };
+    auto bail = [&](lbm_status s2) {
+        g_create_err = c->err.empty() ? std::string("lbm_create failed") : c->err;
+        cudaStreamSynchronize(c->stream);
+        cleanup();
+        lbm_destroy(c);
+        return s2;
+    };
+#define LBM_CREATE_CUDA(call)                                              \
+    do {                                                                   \
+        cudaError_t _e = (call);                                           \
+        if (_e != cudaSuccess) return bail(cuda_fail(c, #call, _e));       \
+    } while (0)
+
+    const int64_t N = (int64_t)nx * ny * nz;
+    if (on_device) {
+        d_nt = const_cast<uint8_t*>(node_type);
+    } else {
+        LBM_CREATE_CUDA(dev_alloc(&d_nt, (size_t)N));
+        LBM_CREATE_CUDA(cudaMemcpyAsync(d_nt, node_type, (size_t)N, cudaMemcpyHostToDevice, c->stream));
+    }
+    const int64_t nb = lbm::scan_block_count(nT);
+    LBM_CREATE_CUDA(dev_alloc(&c->tile_map, (size_t)nT));
+    LBM_CREATE_CUDA(dev_alloc(&c->non_empty, (size_t)nT));
+    LBM_CREATE_CUDA(dev_alloc(&d_flag, (size_t)nT));
+    LBM_CREATE_CUDA(dev_alloc(&d_sums, (size_t)nb));
+    LBM_CREATE_CUDA(dev_alloc(&d_count, 1));
+    LBM_CREATE_CUDA(dev_alloc(&d_bad, 1));
+    LBM_CREATE_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+    LBM_CREATE_CUDA(lbm::launch_tile_flags(d_nt, nx, ny, nz, c->Tx, c->Ty, c->Tz, d_flag, d_bad, c->stream));
+    LBM_CREATE_CUDA(lbm::launch_scan_flags(d_flag, nT, c->tile_map, c->non_empty, d_count, d_sums, nb, c->stream));
+    int64_t count = 0;
+    int bad = 0;
+    LBM_CREATE_CUDA(cudaMemcpyAsync(&count, d_count, sizeof(count), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CREATE_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) {
+        fail(c, LBM_EINVAL, "node_type holds values other than 0 (solid), 1 (fluid), 2 (inlet), 3 (outlet)");
+        return bail(LBM_EINVAL);
+    }
+    if (count < 0 || count > nT) {
+        fail(c, LBM_EINTERNAL, "tile count out of range");
+        return bail(LBM_EINTERNAL);
+    }
+    c->n_tiles = count;
+    const size_t copy_bytes = (size_t)count * lbm::Q * lbm::SLOTS * lbm::dtype_size(dtype);
+    c->n_partials = lbm::reduce_blocks(count);
+    LBM_CREATE_CUDA(dev_alloc(&c->nbr, (size_t)count * lbm::NBR));
+    LBM_CREATE_CUDA(dev_alloc(&c->smask, (size_t)count));
+    LBM_CREATE_CUDA(dev_alloc(&c->tflags, (size_t)count));
+    LBM_CREATE_CUDA(dev_alloc(&c->ntype, (size_t)count * lbm::SLOTS));
+    LBM_CREATE_CUDA(dev_alloc(&c->partials, (size_t)c->n_partials * 4));
+    LBM_CREATE_CUDA(dev_alloc(&c->d_out, 8));
+    LBM_CREATE_CUDA(cudaMalloc(&c->f[0], std::max<size_t>(copy_bytes, 16)));
+    LBM_CREATE_CUDA(cudaMalloc(&c->f[1], std::max<size_t>(copy_bytes, 16)));
+    LBM_CREATE_CUDA(lbm::launch_tile_meta(c, d_nt));
+    unsigned long long nonsolid = 0;
+    LBM_CREATE_CUDA(cudaMemcpyAsync(&nonsolid, c->d_out, sizeof(nonsolid), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CREATE_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
+    if (count > 0) {
+        k_check_nbr<<<152 * 4, 256, 0, c->stream>>>(c->nbr, count * lbm::NBR, count, d_bad);
+        LBM_CREATE_CUDA(cudaGetLastError());
+    }
+    LBM_CREATE_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
+    if (bad) {
+        fail(c, LBM_EINTERNAL, "neighbour table holds an out-of-range tile rank");
+        return bail(LBM_EINTERNAL);
+    }
+    c->n_nonsolid = (int64_t)nonsolid;
+    c->p.omega = 1.0;
+    c->p.beta = 0.5;
+    c->p.rho_out = 1.0;
+    cleanup();
+#undef LBM_CREATE_CUDA
+    *out = c;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double* g_field,
+                          int g_field_on_device, const double* u_in, double rho_out) {
+    LBM_CHECK_CTX(c);
+    if (!(std::isfinite(tau) && tau > 0.5)) return fail(c, LBM_EINVAL, "tau must be finite and > 1/2");
+    if (!finite3(g) || !finite3(u_in)) return fail(c, LBM_EINVAL, "g and u_in must be finite");
+    if (!(std::isfinite(rho_out) && rho_out > 0.0)) return fail(c, LBM_EINVAL, "rho_out must be finite and > 0");
+    if (g_field) {
+        const int64_t N = (int64_t)c->nx * c->ny * c->nz;
+        const size_t gbytes = (size_t)std::max<int64_t>(c->n_tiles, 1) * lbm::SLOTS * (c->dtype == LBM_F64 ? 8 : 4);
+        if (!c->gfield) LBM_CUDA(c, cudaMalloc(&c->gfield, gbytes));
+        const double* d_dense = g_field;
+        double* tmp = nullptr;
+        if (!g_field_on_device) {
+            LBM_CUDA(c, dev_alloc(&tmp, (size_t)N));
+            cudaError_t e = cudaMemcpyAsync(tmp, g_field, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+            if (e != cudaSuccess) {
+                cudaFree(tmp);
+                return cuda_fail(c, "cudaMemcpyAsync(g_field)", e);
+            }
+            d_dense = tmp;
+        }
+        cudaError_t e = c->n_tiles > 0 ? lbm::launch_gfield(c, d_dense) : cudaSuccess;
+        if (tmp) {
+            cudaError_t e2 = cudaStreamSynchronize(c->stream);
+            cudaFree(tmp);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e != cudaSuccess) return cuda_fail(c, "set g_field", e);
+    } else if (c->gfield) {
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+        cudaFree(c->gfield);
+        c->gfield = nullptr;
+    }
+    c->tau = tau;
+    c->p.omega = 1.0 / tau;
+    c->p.beta = 1.0 - 0.5 / tau;
+    for (int a = 0; a < 3; a++) {
+        c->p.g[a] = g ? g[a] : 0.0;
+        c->p.u_in[a] = u_in ? u_in[a] : 0.0;
+    }
+    c->p.rho_out = rho_out;
+    c->p.gfield = c->gfield;
+    c->params_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx* c, double rho0, const double* u0) {
+    LBM_CHECK_CTX(c);
+    if (!(std::isfinite(rho0) && rho0 > 0.0) || !finite3(u0)) return fail(c, LBM_EINVAL, "rho0 must be > 0, u0 finite");
+    const double z[3] = {0.0, 0.0, 0.0};
+    if (c->n_tiles > 0) LBM_CUDA(c, lbm::launch_init(c, rho0, u0 ? u0 : z));
+    c->cur = 0;
+    c->state_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int n) {
+    LBM_CHECK_CTX(c);
+    if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (!c->state_set || !c->params_set) return fail(c, LBM_ESTATE, "set parameters and a state before stepping");
+    for (int k = 0; k < n; k++) {
+        LBM_CUDA(c, lbm::launch_step(c, c->f[c->cur], c->f[1 - c->cur]));
+        c->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_reduce(lbm_ctx* c, double* mass, double* momentum) {
+    LBM_CHECK_CTX(c);
+    if (!c->state_set) return fail(c, LBM_ESTATE, "no state");
+    double h[4] = {0.0, 0.0, 0.0, 0.0};
+    if (c->n_tiles > 0) {
+        LBM_CUDA(c, lbm::launch_reduce(c, c->d_out));
+        LBM_CUDA(c, cudaMemcpyAsync(h, c->d_out, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    if (mass) *mass = h[0];
+    if (momentum)
+        for (int a = 0; a < 3; a++) momentum[a] = h[1 + a];
+    if (!std::isfinite(h[0])) return fail(c, LBM_ENONFINITE, "mass is not finite");
+    return LBM_OK;
+}
+
+lbm_status lbm_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64, int on_device) {
+    LBM_CHECK_CTX(c);
+    if (!rho || !u) return fail(c, LBM_EINVAL, "rho and u are required");
+    if (!c->state_set) return fail(c, LBM_ESTATE, "no state");
+    const int64_t N = (int64_t)c->nx * c->ny * c->nz;
+    const size_t es = out_f64 ? 8 : 4;
+    void* d_rho = rho;
+    void* d_u = u;
+    void* tmp = nullptr;
+    if (!on_device) {
+        LBM_CUDA(c, cudaMalloc(&tmp, (size_t)N * 4 * es));
+        d_rho = tmp;
+        d_u = static_cast<char*>(tmp) + (size_t)N * es;
+    }
+    cudaError_t e = cudaMemsetAsync(d_rho, 0, (size_t)N * es, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_u, 0, (size_t)N * 3 * es, c->stream);
+    if (e == cudaSuccess) e = lbm::launch_macroscopic(c, d_rho, d_u, out_f64);
+    if (e == cudaSuccess && !on_device) {
+        e = cudaMemcpyAsync(rho, d_rho, (size_t)N * es, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(u, d_u, (size_t)N * 3 * es, cudaMemcpyDeviceToHost, c->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    }
+    if (tmp) {
+        if (e != cudaSuccess) cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, "lbm_macroscopic", e);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_f_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* out) {
+    LBM_CHECK_CTX(c);
+    if (!out || bx < 1 || by < 1 || bz < 1) return fail(c, LBM_EINVAL, "bad box");
+    if (!c->state_set) return fail(c, LBM_ESTATE, "no state");
+    const int64_t B = (int64_t)bx * by * bz;
+    double* tmp = nullptr;
+    LBM_CUDA(c, dev_alloc(&tmp, (size_t)B * lbm::Q));
+    cudaError_t e = lbm::launch_get_box(c, x0, y0, z0, bx, by, bz, tmp);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, (size_t)B * lbm::Q * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
+    cudaError_t e2 = cudaStreamSynchronize(c->stream);
+    cudaFree(tmp);
+    if (e == cudaSuccess) e = e2;
+    if (e != cudaSuccess) return cuda_fail(c, "lbm_get_f_box", e);
+    return LBM_OK;
+}
+
+lbm_status lbm_get_f(lbm_ctx* c, double* f_dense) {
+    LBM_CHECK_CTX(c);
+    return lbm_get_f_box(c, 0, 0, 0, c->nx, c->ny, c->nz, f_dense);
+}
+
+lbm_status lbm_set_f(lbm_ctx* c, const double* f_dense) {
+    LBM_CHECK_CTX(c);
+    if (!f_dense) return fail(c, LBM_EINVAL, "f_dense is NULL");
+    const int64_t N = (int64_t)c->nx * c->ny * c->nz;
+    if (c->n_tiles > 0) {
+        double* tmp = nullptr;
+        LBM_CUDA(c, dev_alloc(&tmp, (size_t)N * lbm::Q));
+        cudaError_t e = cudaMemcpyAsync(tmp, f_dense, (size_t)N * lbm::Q * sizeof(double), cudaMemcpyHostToDevice, c->stream);
+        if (e == cudaSuccess) e = lbm::launch_set_dense(c, tmp);
+        cudaError_t e2 = cudaStreamSynchronize(c->stream);
+        cudaFree(tmp);
+        if (e == cudaSuccess) e = e2;
+        if (e != cudaSuccess) return cuda_fail(c, "lbm_set_f", e);
+    }
+    c->state_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_tiles(lbm_ctx* c, int32_t* tile_map, uint32_t* non_empty, int64_t* n_tiles) {
+    LBM_CHECK_CTX(c);
+    if (n_tiles) *n_tiles = c->n_tiles;
+    const size_t nT = (size_t)c->Tx * c->Ty * c->Tz;
+    if (tile_map) LBM_CUDA(c, cudaMemcpyAsync(tile_map, c->tile_map, nT * sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream));
+    if (non_empty && c->n_tiles > 0)
+        LBM_CUDA(c, cudaMemcpyAsync(non_empty, c->non_empty, (size_t)c->n_tiles * sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_ctx* c, int64_t* n_tiles, int64_t* n_nonsolid, int64_t* copy_bytes) {
+    LBM_CHECK_CTX(c);
+    if (n_tiles) *n_tiles = c->n_tiles;
+    if (n_nonsolid) *n_nonsolid = c->n_nonsolid;
+    if (copy_bytes) *copy_bytes = c->n_tiles * lbm::Q * lbm::SLOTS * (int64_t)lbm::dtype_size(c->dtype);
+    return LBM_OK;
+}
+
+lbm_status lbm_save_state(lbm_ctx* c, void* blob, size_t* nbytes) {
+    LBM_CHECK_CTX(c);
+    if (!nbytes) return fail(c, LBM_EINVAL, "nbytes is NULL");
+    const size_t payload = (size_t)c->n_tiles * lbm::Q * lbm::SLOTS * lbm::dtype_size(c->dtype);
+    const size_t total = sizeof(StateHeader) + payload;
+    if (!blob) {
+        *nbytes = total;
+        return LBM_OK;
+    }
+    if (*nbytes < total) return fail(c, LBM_EINVAL, "blob too small");
+    if (!c->state_set) return fail(c, LBM_ESTATE, "no state");
+    StateHeader h{};
+    std::memcpy(h.magic, "LBMGB300", 8);
+    h.version = 1;
+    h.dtype = c->dtype;
+    h.nx = c->nx; h.ny = c->ny; h.nz = c->nz;
+    h.periodic = c->periodic;
+    h.n_tiles = c->n_tiles;
+    lbm_status st = geometry_hash(c, &h.geometry_hash);
+    if (st != LBM_OK) return st;
+    h.payload_bytes = payload;
+    char* dst = static_cast<char*>(blob) + sizeof(StateHeader);
+    if (payload > 0) {
+        LBM_CUDA(c, cudaMemcpyAsync(dst, c->f[c->cur], payload, cudaMemcpyDeviceToHost, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    h.payload_hash = fnv1a(dst, payload);
+    std::memcpy(blob, &h, sizeof(h));
+    *nbytes = total;
+    return LBM_OK;
+}
+
+lbm_status lbm_load_state(lbm_ctx* c, const void* blob, size_t nbytes) {
+    LBM_CHECK_CTX(c);
+    if (!blob || nbytes < sizeof(StateHeader)) return fail(c, LBM_ESTATE, "blob too small");
+    StateHeader h;
+    std::memcpy(&h, blob, sizeof(h));
+    const size_t payload = (size_t)c->n_tiles * lbm::Q * lbm::SLOTS * lbm::dtype_size(c->dtype);
+    if (std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) return fail(c, LBM_ESTATE, "not a state blob");
+    if (h.dtype != c->dtype || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.periodic != c->periodic ||
+        h.n_tiles != c->n_tiles || h.payload_bytes != payload || nbytes < sizeof(h) + payload)
+        return fail(c, LBM_ESTATE, "state blob is for another geometry or dtype");
+    const char* src = static_cast<const char*>(blob) + sizeof(StateHeader);
+    if (fnv1a(src, payload) != h.payload_hash) return fail(c, LBM_ESTATE, "state blob checksum mismatch");
+    uint64_t gh = 0;
+    lbm_status st = geometry_hash(c, &gh);
+    if (st != LBM_OK) return st;
+    if (gh != h.geometry_hash) return fail(c, LBM_ESTATE, "state blob geometry hash mismatch");
+    if (payload > 0) {
+        LBM_CUDA(c, cudaMemcpyAsync(c->f[c->cur], src, payload, cudaMemcpyHostToDevice, c->stream));
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    }
+    c->state_set = true;
+    return LBM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,137 @@
+// lbm_internal.cuh -- definitions shared by the translation units of liblbm_gb300.
+//
+// Device data layout (all in HBM, allocated once per context):
+//   tile_map [Tz*Ty*Tx]  int32   rank of a kept tile, or -1 (Sec. 3.1 tileMap)
+//   non_empty[n_tiles]   uint32  linear tile index t = tx + Tx (ty + Ty tz) (nonEmptyTiles)
+//   nbr      [n_tiles][27] int32 ranks of the 3x3x3 tile neighbourhood, index
+//                               13 + dx + 3 dy + 9 dz, -1 for dropped or out-of-box tiles
+//                               (the local tileMap copy of Sec. 3.4, precomputed once)
+//   smask    [n_tiles]   uint64  bit s set when node s of the tile is solid or padding
+//   tflags   [n_tiles]   uint32  bit 0: the tile holds inlet or outlet nodes
+//   ntype    [n_tiles][64] uint8 node types in slot order (the per-tile nodeType block)
+//   f[2]     [n_tiles][19][64]   populations, tile-major SoA: one 64-value data block
+//                               per direction per tile (Sec. 3.2, Fig. 3), slot
+//                               s = x + 4 y + 16 z inside the tile (Eq. 11 order)
+//   gfield   [n_tiles][64]       optional per-node x force (double for F64, else float)
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int Q = 19;
+constexpr int TILE = 4;
+constexpr int SLOTS = 64;
+constexpr int NBR = 27;
+constexpr int FLAG_HAS_BC = 1;
+// F16S storage scale: h is stored as half(h * 2^12), so |h| in [1.5e-8, 16] is normal.
+constexpr float F16_SCALE = 4096.0f;
+constexpr float F16_INV_SCALE = 1.0f / 4096.0f;
+
+// D3Q19 velocities in the numbering documented in lbm.h, weights of Sec. 2.2.
+__host__ __device__ constexpr int cx(int i) {
+    return (i == 1 || i == 7 || i == 10 || i == 11 || i == 12) ? 1
+         : (i == 3 || i == 8 || i == 9 || i == 13 || i == 14) ? -1 : 0;
+}
+__host__ __device__ constexpr int cy(int i) {
+    return (i == 2 || i == 7 || i == 8 || i == 15 || i == 16) ? 1
+         : (i == 4 || i == 9 || i == 10 || i == 17 || i == 18) ? -1 : 0;
+}
+__host__ __device__ constexpr int cz(int i) {
+    return (i == 5 || i == 11 || i == 13 || i == 15 || i == 17) ? 1
+         : (i == 6 || i == 12 || i == 14 || i == 16 || i == 18) ? -1 : 0;
+}
+// Opposite direction (c_inv(i) = -c_i): 1<->3, 2<->4, 5<->6, 7<->9, 8<->10, 11<->14,
+// 12<->13, 15<->18, 16<->17; constexpr so that it folds after unrolling.
+__host__ __device__ constexpr int inv(int i) {
+    return i == 1 ? 3 : i == 3 ? 1 : i == 2 ? 4 : i == 4 ? 2 : i == 5 ? 6 : i == 6 ? 5
+         : i == 7 ? 9 : i == 9 ? 7 : i == 8 ? 10 : i == 10 ? 8 : i == 11 ? 14 : i == 14 ? 11
+         : i == 12 ? 13 : i == 13 ? 12 : i == 15 ? 18 : i == 18 ? 15 : i == 16 ? 17
+         : i == 17 ? 16 : 0;
+}
+__host__ __device__ constexpr double wgt(int i) {
+    return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Storage traits: element type T in HBM and arithmetic type R.
+template <int DT> struct Store;
+template <> struct Store<LBM_F64> {
+    using T = double;
+    using R = double;
+    static constexpr bool SHIFT = false;   // arithmetic on f itself
+};
+template <> struct Store<LBM_F32> {
+    using T = float;
+    using R = float;
+    static constexpr bool SHIFT = true;    // arithmetic on h = f - w, stored as f
+};
+template <> struct Store<LBM_F16S> {
+    using T = __half;
+    using R = float;
+    static constexpr bool SHIFT = true;    // arithmetic and storage on h = f - w
+};
+
+inline size_t dtype_size(int dt) { return dt == LBM_F64 ? 8 : dt == LBM_F32 ? 4 : 2; }
+
+struct StepParams {
+    double omega;   // 1/tau
+    double beta;    // 1 - 1/(2 tau), Guo prefactor
+    double g[3];
+    double u_in[3];
+    double rho_out;
+    const void* gfield;
+};
+
+}  // namespace lbm
+
+struct lbm_ctx {
+    int nx = 0, ny = 0, nz = 0, Tx = 0, Ty = 0, Tz = 0;
+    unsigned periodic = 0;
+    int dtype = LBM_F64;
+    int64_t n_tiles = 0, n_nonsolid = 0;
+    cudaStream_t stream = nullptr;
+    int32_t* tile_map = nullptr;
+    uint32_t* non_empty = nullptr;
+    int32_t* nbr = nullptr;
+    uint64_t* smask = nullptr;
+    uint32_t* tflags = nullptr;
+    uint8_t* ntype = nullptr;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;
+    void* gfield = nullptr;
+    bool params_set = false;
+    bool state_set = false;
+    lbm::StepParams p{};
+    double tau = 0.0;
+    // reduction scratch
+    double* partials = nullptr;
+    double* d_out = nullptr;
+    int n_partials = 0;
+    uint64_t geometry_hash = 0;
+    lbm_status sticky = LBM_OK;
+    std::string err;
+};
+
+namespace lbm {
+// Launchers (defined in lbm_tiles.cu / lbm_step.cu); all queue work on ctx->stream and
+// return cudaGetLastError() of the launch.
+cudaError_t launch_tile_flags(const uint8_t* nt, int nx, int ny, int nz, int Tx, int Ty, int Tz,
+                              uint8_t* flag, int* bad, cudaStream_t st);
+cudaError_t launch_scan_flags(const uint8_t* flag, int64_t n, int32_t* tile_map, uint32_t* non_empty,
+                              int64_t* d_count, int64_t* block_sums, int64_t nblocks, cudaStream_t st);
+int64_t scan_block_count(int64_t n);
+cudaError_t launch_tile_meta(lbm_ctx* c, const uint8_t* nt);
+cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]);
+cudaError_t launch_step(lbm_ctx* c, const void* A, void* B);
+cudaError_t launch_reduce(lbm_ctx* c, double* d_out);
+cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64);
+cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* d_out);
+cudaError_t launch_set_dense(lbm_ctx* c, const double* d_dense);
+cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense);
+}  // namespace lbm

@@ -1,0 +1,506 @@
+// lbm_tiles.cu -- tile-map builder (Algorithm 1 on the GPU), per-tile metadata,
+// equilibrium initialisation, FP64 invariant reduction, macroscopic export and the
+// dense <-> tile-major conversions of liblbm_gb300.
+#include <algorithm>
+
+#include "lbm_internal.cuh"
+#include "lbm_store.cuh"
+
+namespace lbm {
+
+// ----------------------------------------------------------------------------------
+// Algorithm 1 (Sec. 3.1) as flag -> exclusive scan -> scatter. The scan runs over the
+// linear tile index t = tx + Tx (ty + Ty tz), which is the loop order of Algorithm 1,
+// so ranks equal the paper's discovery order.
+
+// flag[t] = 1 when some node of tile t is not solid; padding nodes count as solid.
+__global__ void k_tile_flags(const uint8_t* __restrict__ nt, int nx, int ny, int nz, int Tx, int Ty,
+                             int Tz, uint8_t* __restrict__ flag, int* __restrict__ bad) {
+    const int64_t nT = (int64_t)Tx * Ty * Tz;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nT;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int tx = (int)(t % Tx);
+        const int64_t r = t / Tx;
+        const int ty = (int)(r % Ty);
+        const int tz = (int)(r / Ty);
+        int any = 0, badv = 0;
+        for (int dz = 0; dz < TILE; dz++) {
+            const int z = TILE * tz + dz;
+            if (z >= nz) break;
+            for (int dy = 0; dy < TILE; dy++) {
+                const int y = TILE * ty + dy;
+                if (y >= ny) break;
+                const uint8_t* row = nt + ((int64_t)z * ny + y) * nx;
+                for (int dx = 0; dx < TILE; dx++) {
+                    const int x = TILE * tx + dx;
+                    if (x >= nx) break;
+                    const uint8_t v = row[x];
+                    any |= (v != LBM_SOLID);
+                    badv |= (v > LBM_OUTLET);
+                }
+            }
+        }
+        flag[t] = (uint8_t)any;
+        if (badv) atomicOr(bad, 1);
+    }
+}
+
+constexpr int SCAN_BLOCK = 1024;
+
+// Exclusive prefix sum of v over the 1024 threads of a block; *total gets the sum.
+__device__ int64_t block_exclusive_scan(int64_t v, int64_t* total) {
+    __shared__ int64_t warp_sums[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int64_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_sums[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t s = warp_sums[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int64_t y = __shfl_up_sync(0xffffffffu, s, o);
+            if (lane >= o) s += y;
+        }
+        warp_sums[lane] = s;   // inclusive over warps
+    }
+    __syncthreads();
+    const int64_t before = (warp > 0 ? warp_sums[warp - 1] : 0) + x - v;
+    *total = warp_sums[31];
+    __syncthreads();
+    return before;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_sums(const uint8_t* __restrict__ flag, int64_t n,
+                                                          int64_t* __restrict__ block_sums) {
+    const int64_t t = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x;
+    const int64_t v = t < n ? flag[t] : 0;
+    int64_t total;
+    block_exclusive_scan(v, &total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// One block: exclusive scan of the block sums in chunks of 1024 with a running carry.
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_top(int64_t* __restrict__ block_sums, int64_t nb,
+                                                         int64_t* __restrict__ d_count) {
+    int64_t carry = 0;
+    for (int64_t base = 0; base < nb; base += SCAN_BLOCK) {
+        const int64_t i = base + threadIdx.x;
+        const int64_t v = i < nb ? block_sums[i] : 0;
+        int64_t total;
+        const int64_t ex = block_exclusive_scan(v, &total);
+        if (i < nb) block_sums[i] = carry + ex;
+        carry += total;
+    }
+    if (threadIdx.x == 0) *d_count = carry;
+}
+
+__global__ void __launch_bounds__(SCAN_BLOCK) k_scan_scatter(const uint8_t* __restrict__ flag, int64_t n,
+                                                             const int64_t* __restrict__ block_off,
+                                                             int32_t* __restrict__ tile_map,
+                                                             uint32_t* __restrict__ non_empty) {
+    const int64_t t = blockIdx.x * (int64_t)SCAN_BLOCK + threadIdx.x;
+    const int64_t v = t < n ? flag[t] : 0;
+    int64_t total;
+    const int64_t rank = block_off[blockIdx.x] + block_exclusive_scan(v, &total);
+    if (t < n) {
+        tile_map[t] = v ? (int32_t)rank : -1;
+        if (v) non_empty[rank] = (uint32_t)t;
+    }
+}
+
+int64_t scan_block_count(int64_t n) { return (n + SCAN_BLOCK - 1) / SCAN_BLOCK; }
+
+cudaError_t launch_tile_flags(const uint8_t* nt, int nx, int ny, int nz, int Tx, int Ty, int Tz,
+                              uint8_t* flag, int* bad, cudaStream_t st) {
+    const int64_t nT = (int64_t)Tx * Ty * Tz;
+    const int64_t blocks = std::min<int64_t>((nT + 255) / 256, 152 * 64);
+    k_tile_flags<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(nt, nx, ny, nz, Tx, Ty, Tz, flag, bad);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan_flags(const uint8_t* flag, int64_t n, int32_t* tile_map, uint32_t* non_empty,
+                              int64_t* d_count, int64_t* block_sums, int64_t nblocks, cudaStream_t st) {
+    k_scan_sums<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(flag, n, block_sums);
+    k_scan_top<<<1, SCAN_BLOCK, 0, st>>>(block_sums, nblocks, d_count);
+    k_scan_scatter<<<(unsigned)nblocks, SCAN_BLOCK, 0, st>>>(flag, n, block_sums, tile_map, non_empty);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Per-tile metadata: node types in slot order, the solid mask, the boundary flag and
+// the 3x3x3 neighbourhood of tile ranks (the local tileMap copy of Sec. 3.4), wrapped on
+// periodic axes. One 64-thread block per kept tile, thread s = slot s.
+__global__ void __launch_bounds__(64) k_tile_meta(const uint8_t* __restrict__ nt, int nx, int ny, int nz,
+                                                  int Tx, int Ty, int Tz, unsigned periodic,
+                                                  const int32_t* __restrict__ tile_map,
+                                                  const uint32_t* __restrict__ non_empty, int64_t n_tiles,
+                                                  int32_t* __restrict__ nbr, uint64_t* __restrict__ smask,
+                                                  uint32_t* __restrict__ tflags, uint8_t* __restrict__ ntype,
+                                                  unsigned long long* __restrict__ n_nonsolid) {
+    __shared__ uint32_t s_solid[2], s_bc[2];
+    const int s = threadIdx.x, lane = s & 31, warp = s >> 5;
+    for (int64_t k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+        const uint32_t t = non_empty[k];
+        const int tx = (int)(t % (uint32_t)Tx);
+        const int ty = (int)((t / (uint32_t)Tx) % (uint32_t)Ty);
+        const int tz = (int)(t / ((uint32_t)Tx * (uint32_t)Ty));
+        const int x = TILE * tx + (s & 3), y = TILE * ty + ((s >> 2) & 3), z = TILE * tz + (s >> 4);
+        uint8_t v = LBM_SOLID;
+        if (x < nx && y < ny && z < nz) v = nt[x + (int64_t)nx * (y + (int64_t)ny * z)];
+        ntype[k * SLOTS + s] = v;
+        const uint32_t solid_bits = __ballot_sync(0xffffffffu, v == LBM_SOLID);
+        const uint32_t bc_bits = __ballot_sync(0xffffffffu, v == LBM_INLET || v == LBM_OUTLET);
+        if (lane == 0) {
+            s_solid[warp] = solid_bits;
+            s_bc[warp] = bc_bits;
+            atomicAdd(n_nonsolid, (unsigned long long)(32 - __popc(solid_bits)));
+        }
+        if (s < NBR) {
+            const int d[3] = {s % 3 - 1, (s / 3) % 3 - 1, s / 9 - 1};
+            int c[3] = {tx + d[0], ty + d[1], tz + d[2]};
+            const int T[3] = {Tx, Ty, Tz};
+            bool inside = true;
+            for (int a = 0; a < 3; a++) {
+                if (c[a] < 0 || c[a] >= T[a]) {
+                    if (periodic & (1u << a)) c[a] = (c[a] + T[a]) % T[a];
+                    else inside = false;
+                }
+            }
+            nbr[k * NBR + s] = inside ? tile_map[c[0] + (int64_t)Tx * (c[1] + (int64_t)Ty * c[2])] : -1;
+        }
+        __syncthreads();
+        if (s == 0) {
+            smask[k] = (uint64_t)s_solid[0] | ((uint64_t)s_solid[1] << 32);
+            tflags[k] = (s_bc[0] | s_bc[1]) ? FLAG_HAS_BC : 0;
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t launch_tile_meta(lbm_ctx* c, const uint8_t* nt) {
+    unsigned long long* d_cnt = reinterpret_cast<unsigned long long*>(c->d_out);
+    cudaError_t e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), c->stream);
+    if (e != cudaSuccess) return e;
+    const int64_t blocks = std::min<int64_t>(c->n_tiles, 1 << 20);
+    if (blocks > 0)
+        k_tile_meta<<<(unsigned)blocks, 64, 0, c->stream>>>(nt, c->nx, c->ny, c->nz, c->Tx, c->Ty, c->Tz,
+                                                            c->periodic, c->tile_map, c->non_empty,
+                                                            c->n_tiles, c->nbr, c->smask, c->tflags,
+                                                            c->ntype, d_cnt);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Equilibrium initial state f = f^eq(rho0, u0) (Eq. 3) in both copies; solid slots hold
+// NaN so that any read of one would show in the results.
+template <int DT>
+__global__ void k_init(typename Store<DT>::T* __restrict__ f0, typename Store<DT>::T* __restrict__ f1,
+                       const uint64_t* __restrict__ smask, int64_t n_tiles, double rho0, double ux,
+                       double uy, double uz) {
+    using T = typename Store<DT>::T;
+    const int64_t n = n_tiles * SLOTS;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx >> 6;
+        const int s = (int)(idx & 63);
+        const bool solid = (smask[k] >> s) & 1;
+        const double uu = ux * ux + uy * uy + uz * uz;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
+            const double fe = wgt(i) * rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            const T v = solid ? nan_value<DT>() : from_f64<DT>(fe, i);
+            f0[(k * Q + i) * SLOTS + s] = v;
+            f1[(k * Q + i) * SLOTS + s] = v;
+        }
+    }
+}
+
+static unsigned grid_for(int64_t n, int threads) {
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 32));
+}
+
+cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]) {
+    const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
+    switch (c->dtype) {
+        case LBM_F64:
+            k_init<LBM_F64><<<g, 256, 0, c->stream>>>((double*)c->f[0], (double*)c->f[1], c->smask,
+                                                      c->n_tiles, rho0, u0[0], u0[1], u0[2]);
+            break;
+        case LBM_F32:
+            k_init<LBM_F32><<<g, 256, 0, c->stream>>>((float*)c->f[0], (float*)c->f[1], c->smask,
+                                                      c->n_tiles, rho0, u0[0], u0[1], u0[2]);
+            break;
+        default:
+            k_init<LBM_F16S><<<g, 256, 0, c->stream>>>((__half*)c->f[0], (__half*)c->f[1], c->smask,
+                                                       c->n_tiles, rho0, u0[0], u0[1], u0[2]);
+    }
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// FP64 mass and momentum: per-thread FP64 partials -> warp shuffle tree -> one partial
+// per block -> a fixed-order single-block pass. No atomics, so the result depends only
+// on the launch shape, which is fixed per context.
+constexpr int RED_THREADS = 256;
+
+template <int DT>
+__global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Store<DT>::T* __restrict__ f,
+                                                        const uint64_t* __restrict__ smask,
+                                                        const void* __restrict__ gfield, int64_t n_tiles,
+                                                        StepParams p, double* __restrict__ partials) {
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    const int64_t n = n_tiles * SLOTS;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx >> 6;
+        const int s = (int)(idx & 63);
+        if ((smask[k] >> s) & 1) continue;
+        double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const double v = to_f64<DT>(f[(k * Q + i) * SLOTS + s], i);
+            r += v;
+            jx += cx(i) * v;
+            jy += cy(i) * v;
+            jz += cz(i) * v;
+        }
+        const double Fx = gfield ? gfield_at<DT>(gfield, idx) : p.g[0];
+        acc[0] += r;
+        acc[1] += jx - 0.5 * Fx;
+        acc[2] += jy - 0.5 * p.g[1];
+        acc[3] += jz - 0.5 * p.g[2];
+    }
+    __shared__ double sh[RED_THREADS / 32][4];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int c = 0; c < 4; c++) {
+        double v = acc[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) sh[warp][c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double v = 0.0;
+        for (int w = 0; w < RED_THREADS / 32; w++) v += sh[w][threadIdx.x];
+        partials[blockIdx.x * 4 + threadIdx.x] = v;
+    }
+}
+
+__global__ void __launch_bounds__(RED_THREADS) k_reduce_final(const double* __restrict__ partials, int nb,
+                                                              double* __restrict__ out) {
+    __shared__ double sh[RED_THREADS][4];
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int b = threadIdx.x; b < nb; b += RED_THREADS)
+        for (int c = 0; c < 4; c++) acc[c] += partials[b * 4 + c];
+    for (int c = 0; c < 4; c++) sh[threadIdx.x][c] = acc[c];
+    __syncthreads();
+    for (int h = RED_THREADS / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h)
+            for (int c = 0; c < 4; c++) sh[threadIdx.x][c] += sh[threadIdx.x + h][c];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[threadIdx.x] = sh[0][threadIdx.x];
+}
+
+int reduce_blocks(int64_t n_tiles) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n_tiles * SLOTS + RED_THREADS - 1) / RED_THREADS, 152 * 4));
+}
+
+cudaError_t launch_reduce(lbm_ctx* c, double* d_out) {
+    const int nb = c->n_partials;
+    const void* A = c->f[c->cur];
+    switch (c->dtype) {
+        case LBM_F64:
+            k_reduce<LBM_F64><<<nb, RED_THREADS, 0, c->stream>>>((const double*)A, c->smask, c->gfield,
+                                                                 c->n_tiles, c->p, c->partials);
+            break;
+        case LBM_F32:
+            k_reduce<LBM_F32><<<nb, RED_THREADS, 0, c->stream>>>((const float*)A, c->smask, c->gfield,
+                                                                 c->n_tiles, c->p, c->partials);
+            break;
+        default:
+            k_reduce<LBM_F16S><<<nb, RED_THREADS, 0, c->stream>>>((const __half*)A, c->smask, c->gfield,
+                                                                  c->n_tiles, c->p, c->partials);
+    }
+    k_reduce_final<<<1, RED_THREADS, 0, c->stream>>>(c->partials, nb, d_out);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Macroscopic export from the stored post-collision populations: rho = sum f*,
+// u = (sum c f* - F/2)/rho, into dense arrays (already zeroed by the caller).
+template <int DT, typename O>
+__global__ void k_macro(const typename Store<DT>::T* __restrict__ f, const uint64_t* __restrict__ smask,
+                        const uint32_t* __restrict__ non_empty, const void* __restrict__ gfield,
+                        int64_t n_tiles, int nx, int ny, int nz, int Tx, int Ty, StepParams p,
+                        O* __restrict__ rho, O* __restrict__ u) {
+    const int64_t n = n_tiles * SLOTS;
+    const int64_t N = (int64_t)nx * ny * nz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx >> 6;
+        const int s = (int)(idx & 63);
+        if ((smask[k] >> s) & 1) continue;
+        const uint32_t t = non_empty[k];
+        const int x = TILE * (int)(t % (uint32_t)Tx) + (s & 3);
+        const int y = TILE * (int)((t / (uint32_t)Tx) % (uint32_t)Ty) + ((s >> 2) & 3);
+        const int z = TILE * (int)(t / ((uint32_t)Tx * (uint32_t)Ty)) + (s >> 4);
+        const int64_t node = x + (int64_t)nx * (y + (int64_t)ny * z);
+        double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const double v = to_f64<DT>(f[(k * Q + i) * SLOTS + s], i);
+            r += v;
+            jx += cx(i) * v;
+            jy += cy(i) * v;
+            jz += cz(i) * v;
+        }
+        const double Fx = gfield ? gfield_at<DT>(gfield, idx) : p.g[0];
+        rho[node] = (O)r;
+        u[node] = (O)((jx - 0.5 * Fx) / r);
+        u[N + node] = (O)((jy - 0.5 * p.g[1]) / r);
+        u[2 * N + node] = (O)((jz - 0.5 * p.g[2]) / r);
+    }
+}
+
+template <typename O>
+static void macro_dispatch(lbm_ctx* c, const void* A, O* rho, O* u) {
+    const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
+#define LBM_MACRO(DT, TT)                                                                               \
+    k_macro<DT, O><<<g, 256, 0, c->stream>>>((const TT*)A, c->smask, c->non_empty, c->gfield, c->n_tiles, \
+                                             c->nx, c->ny, c->nz, c->Tx, c->Ty, c->p, rho, u)
+    if (c->dtype == LBM_F64) LBM_MACRO(LBM_F64, double);
+    else if (c->dtype == LBM_F32) LBM_MACRO(LBM_F32, float);
+    else LBM_MACRO(LBM_F16S, __half);
+#undef LBM_MACRO
+}
+
+cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64) {
+    if (c->n_tiles == 0) return cudaSuccess;
+    if (out_f64) macro_dispatch<double>(c, c->f[c->cur], (double*)rho, (double*)u);
+    else macro_dispatch<float>(c, c->f[c->cur], (float*)rho, (float*)u);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Box export: out[i][bz][by][bx] in FP64; NaN for solid, dropped or outside nodes.
+template <int DT>
+__global__ void k_get_box(const typename Store<DT>::T* __restrict__ f, const int32_t* __restrict__ tile_map,
+                          const uint64_t* __restrict__ smask, int nx, int ny, int nz, int Tx, int Ty,
+                          unsigned periodic, int x0, int y0, int z0, int bx, int by, int bz,
+                          double* __restrict__ out) {
+    const int64_t B = (int64_t)bx * by * bz;
+    for (int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; b < B;
+         b += (int64_t)gridDim.x * blockDim.x) {
+        int p[3] = {x0 + (int)(b % bx), y0 + (int)((b / bx) % by), z0 + (int)(b / ((int64_t)bx * by))};
+        const int n[3] = {nx, ny, nz};
+        bool inside = true;
+        for (int a = 0; a < 3; a++) {
+            if (p[a] < 0 || p[a] >= n[a]) {
+                if (periodic & (1u << a)) p[a] = ((p[a] % n[a]) + n[a]) % n[a];
+                else inside = false;
+            }
+        }
+        int64_t k = -1;
+        int s = 0;
+        if (inside) {
+            k = tile_map[p[0] / TILE + (int64_t)Tx * (p[1] / TILE + (int64_t)Ty * (p[2] / TILE))];
+            s = (p[0] & 3) + 4 * (p[1] & 3) + 16 * (p[2] & 3);
+            if (k >= 0 && ((smask[k] >> s) & 1)) k = -1;
+        }
+#pragma unroll
+        for (int i = 0; i < Q; i++)
+            out[i * B + b] = k >= 0 ? to_f64<DT>(f[(k * Q + i) * SLOTS + s], i) : __longlong_as_double(0x7ff8000000000000ll);
+    }
+}
+
+cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* d_out) {
+    const unsigned g = grid_for((int64_t)bx * by * bz, 256);
+    const void* A = c->f[c->cur];
+#define LBM_BOX(DT, TT)                                                                                   \
+    k_get_box<DT><<<g, 256, 0, c->stream>>>((const TT*)A, c->tile_map, c->smask, c->nx, c->ny, c->nz, c->Tx, \
+                                            c->Ty, c->periodic, x0, y0, z0, bx, by, bz, d_out)
+    if (c->dtype == LBM_F64) LBM_BOX(LBM_F64, double);
+    else if (c->dtype == LBM_F32) LBM_BOX(LBM_F32, float);
+    else LBM_BOX(LBM_F16S, __half);
+#undef LBM_BOX
+    return cudaGetLastError();
+}
+
+// Dense FP64 import into both copies; solid and padding slots get NaN.
+template <int DT>
+__global__ void k_set_dense(typename Store<DT>::T* __restrict__ f0, typename Store<DT>::T* __restrict__ f1,
+                            const double* __restrict__ dense, const uint64_t* __restrict__ smask,
+                            const uint32_t* __restrict__ non_empty, int64_t n_tiles, int nx, int ny, int nz,
+                            int Tx, int Ty) {
+    using T = typename Store<DT>::T;
+    const int64_t n = n_tiles * SLOTS;
+    const int64_t N = (int64_t)nx * ny * nz;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx >> 6;
+        const int s = (int)(idx & 63);
+        const bool solid = (smask[k] >> s) & 1;
+        const uint32_t t = non_empty[k];
+        const int x = TILE * (int)(t % (uint32_t)Tx) + (s & 3);
+        const int y = TILE * (int)((t / (uint32_t)Tx) % (uint32_t)Ty) + ((s >> 2) & 3);
+        const int z = TILE * (int)(t / ((uint32_t)Tx * (uint32_t)Ty)) + (s >> 4);
+        const int64_t node = solid ? 0 : x + (int64_t)nx * (y + (int64_t)ny * z);
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const T v = solid ? nan_value<DT>() : from_f64<DT>(dense[i * N + node], i);
+            f0[(k * Q + i) * SLOTS + s] = v;
+            f1[(k * Q + i) * SLOTS + s] = v;
+        }
+    }
+}
+
+cudaError_t launch_set_dense(lbm_ctx* c, const double* d_dense) {
+    const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
+#define LBM_SET(DT, TT)                                                                                   \
+    k_set_dense<DT><<<g, 256, 0, c->stream>>>((TT*)c->f[c->cur], (TT*)c->f[1 - c->cur], d_dense, c->smask, \
+                                              c->non_empty, c->n_tiles, c->nx, c->ny, c->nz, c->Tx, c->Ty)
+    if (c->dtype == LBM_F64) LBM_SET(LBM_F64, double);
+    else if (c->dtype == LBM_F32) LBM_SET(LBM_F32, float);
+    else LBM_SET(LBM_F16S, __half);
+#undef LBM_SET
+    return cudaGetLastError();
+}
+
+// Dense per-node x force -> tile-major copy in the arithmetic precision.
+template <typename G>
+__global__ void k_gfield(G* __restrict__ gt, const double* __restrict__ dense, const uint32_t* __restrict__ non_empty,
+                         int64_t n_tiles, int nx, int ny, int nz, int Tx, int Ty) {
+    const int64_t n = n_tiles * SLOTS;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx >> 6;
+        const int s = (int)(idx & 63);
+        const uint32_t t = non_empty[k];
+        const int x = TILE * (int)(t % (uint32_t)Tx) + (s & 3);
+        const int y = TILE * (int)((t / (uint32_t)Tx) % (uint32_t)Ty) + ((s >> 2) & 3);
+        const int z = TILE * (int)(t / ((uint32_t)Tx * (uint32_t)Ty)) + (s >> 4);
+        const bool in = x < nx && y < ny && z < nz;
+        gt[idx] = in ? (G)dense[x + (int64_t)nx * (y + (int64_t)ny * z)] : (G)0;
+    }
+}
+
+cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense) {
+    const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
+    if (c->dtype == LBM_F64)
+        k_gfield<double><<<g, 256, 0, c->stream>>>((double*)c->gfield, d_dense, c->non_empty, c->n_tiles, c->nx,
+                                                   c->ny, c->nz, c->Tx, c->Ty);
+    else
+        k_gfield<float><<<g, 256, 0, c->stream>>>((float*)c->gfield, d_dense, c->non_empty, c->n_tiles, c->nx,
+                                                  c->ny, c->nz, c->Tx, c->Ty);
+    return cudaGetLastError();
+}
+
+}  // namespace lbm

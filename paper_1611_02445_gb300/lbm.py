@@ -1,0 +1,298 @@
+"""Thin ctypes binding of ``liblbm_gb300.so`` (C ABI in ``include/lbm.h``).
+
+Functions keep the C names and only marshal arguments: every step of the computation
+runs in the library's CUDA kernels. There is no CPU fallback: if the library is not
+built, ``load()`` raises. Host arrays are numpy arrays; device arrays are torch CUDA
+tensors (passed by ``data_ptr()``); streams are torch streams or raw ``cudaStream_t``
+integers.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+import re
+
+import numpy as np
+
+from . import build as _build
+
+LBM_F64, LBM_F32, LBM_F16S = 0, 1, 2
+DTYPES = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S}
+SOLID, FLUID, INLET, OUTLET = 0, 1, 2, 3
+PERIODIC_X, PERIODIC_Y, PERIODIC_Z = 1, 2, 4
+STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSUPPORTED",
+          5: "LBM_ESTATE", 6: "LBM_ENONFINITE", 7: "LBM_ETIMEOUT", 8: "LBM_EINTERNAL"}
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
+
+
+class LBMError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Load the CUDA library and declare its signatures; raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build(); "
+                           "this package has no CPU fallback")
+    L = ct.CDLL(path)
+    vp, i, u, d, i64 = ct.c_void_p, ct.c_int, ct.c_uint, ct.c_double, ct.c_int64
+    pd = ct.POINTER(ct.c_double)
+    L.lbm_create.argtypes = [vp, i, i, i, i, i, i, u, vp, ct.POINTER(vp)]
+    L.lbm_destroy.argtypes = [vp]
+    L.lbm_destroy.restype = None
+    L.lbm_last_error.argtypes = [vp]
+    L.lbm_last_error.restype = ct.c_char_p
+    L.lbm_set_stream.argtypes = [vp, vp]
+    L.lbm_set_params.argtypes = [vp, d, pd, vp, i, pd, d]
+    L.lbm_init_equilibrium.argtypes = [vp, d, pd]
+    L.lbm_step.argtypes = [vp, i]
+    L.lbm_macroscopic.argtypes = [vp, vp, vp, i, i]
+    L.lbm_reduce.argtypes = [vp, pd, pd]
+    L.lbm_get_f_box.argtypes = [vp, i, i, i, i, i, i, vp]
+    L.lbm_get_f.argtypes = [vp, vp]
+    L.lbm_set_f.argtypes = [vp, vp]
+    L.lbm_get_tiles.argtypes = [vp, vp, vp, ct.POINTER(i64)]
+    L.lbm_get_info.argtypes = [vp, ct.POINTER(i64), ct.POINTER(i64), ct.POINTER(i64)]
+    L.lbm_save_state.argtypes = [vp, vp, ct.POINTER(ct.c_size_t)]
+    L.lbm_load_state.argtypes = [vp, vp, ct.c_size_t]
+    for name in header_functions():
+        getattr(L, name)   # every declared entry point must be exported
+    _lib = L
+    return L
+
+
+def header_functions():
+    """Names of the functions declared in include/lbm.h."""
+    text = open(HEADER).read()
+    return re.findall(r"^\s*(?:lbm_status|void|const char\s*\*)\s*\**\s*(lbm_\w+)\s*\(", text, re.M)
+
+
+def _ptr(x):
+    """Address of a numpy array, a torch tensor or None."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    return int(x)
+
+
+def _on_device(x) -> int:
+    return int(hasattr(x, "is_cuda") and bool(x.is_cuda))
+
+
+def _d3(v):
+    if v is None:
+        return None
+    a = (ct.c_double * 3)(*[float(t) for t in v])
+    return a
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except Exception:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = load().lbm_last_error(ctx)
+        raise LBMError(status, msg.decode() if msg else "")
+
+
+# ------------------------------------------------------------------ C entry points
+def lbm_create(node_type, nx, ny, nz, tile=4, dtype=LBM_F64, periodic=0, stream=None):
+    L = load()
+    if isinstance(node_type, np.ndarray):
+        node_type = np.ascontiguousarray(node_type, dtype=np.uint8)
+    out = ct.c_void_p()
+    st = L.lbm_create(_ptr(node_type), _on_device(node_type), int(nx), int(ny), int(nz), int(tile),
+                      int(dtype), int(periodic), _stream(stream), ct.byref(out))
+    _check(st, None)
+    return out.value
+
+
+def lbm_destroy(ctx):
+    load().lbm_destroy(ctx)
+
+
+def lbm_last_error(ctx=None) -> str:
+    m = load().lbm_last_error(ctx)
+    return m.decode() if m else ""
+
+
+def lbm_set_stream(ctx, stream):
+    _check(load().lbm_set_stream(ctx, _stream(stream)), ctx)
+
+
+def lbm_set_params(ctx, tau, g=None, g_field=None, u_in=None, rho_out=1.0):
+    if isinstance(g_field, np.ndarray):
+        g_field = np.ascontiguousarray(g_field, dtype=np.float64)
+    _check(load().lbm_set_params(ctx, float(tau), _d3(g), _ptr(g_field), _on_device(g_field), _d3(u_in),
+                                 float(rho_out)), ctx)
+    return g_field
+
+
+def lbm_init_equilibrium(ctx, rho0=1.0, u0=None):
+    _check(load().lbm_init_equilibrium(ctx, float(rho0), _d3(u0)), ctx)
+
+
+def lbm_step(ctx, n=1):
+    _check(load().lbm_step(ctx, int(n)), ctx)
+
+
+def lbm_macroscopic(ctx, rho, u, out_f64=True):
+    """rho, u: numpy arrays (host) or torch CUDA tensors (device) of the dense sizes."""
+    _check(load().lbm_macroscopic(ctx, _ptr(rho), _ptr(u), int(bool(out_f64)), _on_device(rho)), ctx)
+
+
+def lbm_reduce(ctx):
+    m = ct.c_double()
+    p = (ct.c_double * 3)()
+    _check(load().lbm_reduce(ctx, ct.byref(m), p), ctx)
+    return m.value, np.array(list(p))
+
+
+def lbm_get_f_box(ctx, x0, y0, z0, bx, by, bz):
+    out = np.empty((19, bz, by, bx), np.float64)
+    _check(load().lbm_get_f_box(ctx, int(x0), int(y0), int(z0), int(bx), int(by), int(bz), _ptr(out)), ctx)
+    return out
+
+
+def lbm_get_f(ctx, shape):
+    nz, ny, nx = shape
+    out = np.empty((19, nz, ny, nx), np.float64)
+    _check(load().lbm_get_f(ctx, _ptr(out)), ctx)
+    return out
+
+
+def lbm_set_f(ctx, f_dense):
+    f = np.ascontiguousarray(f_dense, dtype=np.float64)
+    _check(load().lbm_set_f(ctx, _ptr(f)), ctx)
+
+
+def lbm_get_info(ctx):
+    a, b, c = ct.c_int64(), ct.c_int64(), ct.c_int64()
+    _check(load().lbm_get_info(ctx, ct.byref(a), ct.byref(b), ct.byref(c)), ctx)
+    return a.value, b.value, c.value
+
+
+def lbm_get_tiles(ctx, tile_grid):
+    """Returns (tile_map [Tz, Ty, Tx] int32, non_empty uint32[n_tiles])."""
+    n = ct.c_int64()
+    _check(load().lbm_get_tiles(ctx, None, None, ct.byref(n)), ctx)
+    tm = np.empty(tile_grid, np.int32)
+    ne = np.empty(max(n.value, 1), np.uint32)
+    _check(load().lbm_get_tiles(ctx, _ptr(tm), _ptr(ne), ct.byref(n)), ctx)
+    return tm, ne[:n.value].copy()
+
+
+def lbm_save_state(ctx) -> bytes:
+    n = ct.c_size_t()
+    _check(load().lbm_save_state(ctx, None, ct.byref(n)), ctx)
+    buf = ct.create_string_buffer(n.value)
+    _check(load().lbm_save_state(ctx, buf, ct.byref(n)), ctx)
+    return buf.raw[:n.value]
+
+
+def lbm_load_state(ctx, blob: bytes):
+    _check(load().lbm_load_state(ctx, blob, len(blob)), ctx)
+
+
+# ------------------------------------------------------------------ convenience class
+class Lattice:
+    """One geometry on the GPU: owns an lbm_ctx and releases it on close()."""
+
+    def __init__(self, node_type, dtype="f64", periodic=0, stream=None):
+        shape = tuple(node_type.shape)
+        self.shape = shape
+        nz, ny, nx = shape
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        self.ctx = lbm_create(node_type, nx, ny, nz, 4, self.dtype, periodic, stream)
+        self.tile_grid = ((nz + 3) // 4, (ny + 3) // 4, (nx + 3) // 4)
+        self._keep = None
+
+    def close(self):
+        if self.ctx:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, tau, g=None, g_field=None, u_in=None, rho_out=1.0):
+        self._keep = lbm_set_params(self.ctx, tau, g, g_field, u_in, rho_out)
+
+    def init_equilibrium(self, rho0=1.0, u0=None):
+        lbm_init_equilibrium(self.ctx, rho0, u0)
+
+    def step(self, n=1):
+        lbm_step(self.ctx, n)
+
+    def set_stream(self, stream):
+        lbm_set_stream(self.ctx, stream)
+
+    def reduce(self):
+        return lbm_reduce(self.ctx)
+
+    def macroscopic(self, out_f64=True):
+        nz, ny, nx = self.shape
+        dt = np.float64 if out_f64 else np.float32
+        rho = np.empty((nz, ny, nx), dt)
+        u = np.empty((3, nz, ny, nx), dt)
+        lbm_macroscopic(self.ctx, rho, u, out_f64)
+        return rho, u
+
+    def get_f(self):
+        return lbm_get_f(self.ctx, self.shape)
+
+    def get_f_box(self, x0, y0, z0, bx, by, bz):
+        return lbm_get_f_box(self.ctx, x0, y0, z0, bx, by, bz)
+
+    def set_f(self, f):
+        lbm_set_f(self.ctx, f)
+
+    def tiles(self):
+        return lbm_get_tiles(self.ctx, self.tile_grid)
+
+    def info(self):
+        n_tiles, n_nonsolid, copy_bytes = lbm_get_info(self.ctx)
+        return {"n_tiles": n_tiles, "n_nonsolid": n_nonsolid, "copy_bytes": copy_bytes,
+                "eta_t": n_nonsolid / (64 * n_tiles) if n_tiles else 0.0}
+
+    def save_state(self) -> bytes:
+        return lbm_save_state(self.ctx)
+
+    def load_state(self, blob: bytes):
+        lbm_load_state(self.ctx, blob)
