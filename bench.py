@@ -164,6 +164,9 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16s"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--size", type=int, default=256,
+                    help="edge of the cubic sphere pack (256 is the benchmark workload; smaller "
+                         "sizes are for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -190,7 +193,7 @@ def main():
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     __graft_entry__.build()
-    nt = I.sphere_pack(256, 8.0, 0.35, I.SEED_POROUS_256)
+    nt = I.sphere_pack(args.size, 8.0, 0.35, I.SEED_POROUS_256)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
 
@@ -256,7 +259,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
-            "config": {"workload": WORKLOAD, "storage": DTYPE_NAME[args.dtype], "n_nonsolid": n_nonsolid,
+            "config": {"workload": WORKLOAD if args.size == 256 else WORKLOAD.replace("256^3", f"{args.size}^3"),
+                       "storage": DTYPE_NAME[args.dtype], "n_nonsolid": n_nonsolid,
                        "n_tiles": info["n_tiles"], "eta_t": info["eta_t"],
                        "state_bytes": 2 * info["copy_bytes"],
                        "l2_policy": "inputs larger than L2 (two population copies of "
@@ -302,9 +306,9 @@ def main():
         dist.destroy_process_group()
 
 
-# Executed FP64 FLOPs per fluid-node update of the FP64 step kernel (2 dfma + dadd + dmul,
-# from an ncu count divided by the non-solid nodes of the launch).
-FP64_FLOPS_PER_NODE = 340
+# Executed FP64 FLOPs per non-solid node update of the FP64 step kernel: ncu counts of
+# 2 * dfma + dadd + dmul over one launch on the 128^3 pack, divided by its 732 512 nodes.
+FP64_FLOPS_PER_NODE = 331
 
 if __name__ == "__main__":
     main()
