@@ -142,6 +142,33 @@ lbm_status lbm_get_info(lbm_ctx* ctx, int64_t* n_tiles, int64_t* n_nonsolid, int
 lbm_status lbm_save_state(lbm_ctx* ctx, void* blob, size_t* nbytes);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* blob, size_t nbytes);
 
+/* Allocation-free tile-map builder. The paper has no counterpart: it builds its tile
+ * map on the host (Sec. 3.1, Algorithm 1) and says nothing about device memory policy.
+ * It is for callers that cannot call cudaMalloc -- code running under a framework whose
+ * caching allocator has reserved the device memory, or hosts that forbid allocation
+ * after start-up -- and that already own their input and output buffers.
+ * It computes what lbm_create builds (tileMap and nonEmptyTiles, bit for bit) but takes
+ * its temporary storage (one flag byte per tile, scan block sums, the count and an
+ * error flag) from one static device array of 4,227,584 bytes that every GPU loading
+ * this library holds until the process exits; it calls no cudaMalloc or cudaFree.
+ *   node_type  device pointer, nx*ny*nz bytes, dense, values 0..3.
+ *   tile_map   device pointer, ceil(nx/4)*ceil(ny/4)*ceil(nz/4) int32 (written in full).
+ *   non_empty  device pointer with room for as many uint32 as tile_map has entries; the
+ *              first *n_tiles are written.
+ *   n_tiles    host pointer; receives the number of kept tiles.
+ *   stream     cudaStream_t for the work; the call synchronises it before returning.
+ * Limits and errors: at most LBM_NOALLOC_MAX_TILES tiles in the tile grid (e.g. a
+ * 1024 x 512 x 512 box); larger grids give LBM_EUNSUPPORTED before any device work.
+ * NULL pointers or dimensions < 1 give LBM_EINVAL, node types outside 0..3 give
+ * LBM_EINVAL after the kernels ran, CUDA failures LBM_ECUDA. There is no message string.
+ * The first call on each device looks up the array's device address (with that device
+ * current); make that first call before any stream capture. All calls share the one
+ * array, so calls whose work overlaps on the GPU (other streams, other host threads)
+ * race and must not be issued. */
+#define LBM_NOALLOC_MAX_TILES (1 << 22)
+lbm_status lbm_build_tiles_noalloc(const uint8_t* node_type, int nx, int ny, int nz, int32_t* tile_map,
+                                   uint32_t* non_empty, int64_t* n_tiles, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -68,6 +68,7 @@ def load():
     L.lbm_get_info.argtypes = [vp, ct.POINTER(i64), ct.POINTER(i64), ct.POINTER(i64)]
     L.lbm_save_state.argtypes = [vp, vp, ct.POINTER(ct.c_size_t)]
     L.lbm_load_state.argtypes = [vp, vp, ct.c_size_t]
+    L.lbm_build_tiles_noalloc.argtypes = [vp, i, i, i, vp, vp, ct.POINTER(i64), vp]
     for name in header_functions():
         getattr(L, name)   # every declared entry point must be exported
     _lib = L
@@ -219,6 +220,26 @@ def lbm_save_state(ctx) -> bytes:
 
 def lbm_load_state(ctx, blob: bytes):
     _check(load().lbm_load_state(ctx, blob, len(blob)), ctx)
+
+
+NOALLOC_MAX_TILES = 1 << 22
+
+
+def lbm_build_tiles_noalloc(node_type, nx, ny, nz, tile_map, non_empty, stream=None):
+    """Tile map into caller-owned device buffers, without any device allocation.
+
+    For callers that cannot allocate device memory themselves (their framework's
+    allocator owns it, or allocation is forbidden after start-up): node_type, tile_map
+    (int32, one entry per tile of the grid) and non_empty (32-bit, as many entries) are
+    device tensors the caller already holds. Returns the number of kept tiles."""
+    n = ct.c_int64()
+    st = load().lbm_build_tiles_noalloc(_ptr(node_type), int(nx), int(ny), int(nz), _ptr(tile_map),
+                                        _ptr(non_empty), ct.byref(n), _stream(stream))
+    if st != 0:
+        hint = {4: f"the tile grid exceeds {NOALLOC_MAX_TILES} tiles held by the static scratch; "
+                   "use lbm_create", 1: "invalid arguments or node types outside 0..3"}.get(st, "")
+        raise LBMError(st, f"lbm_build_tiles_noalloc: {hint}")
+    return n.value
 
 
 # ------------------------------------------------------------------ convenience class
