@@ -63,8 +63,8 @@ cudaError_t dev_alloc(T** p, size_t count) {
 }
 
 void free_all(lbm_ctx* c) {
-    void* bufs[] = {c->tile_map, c->non_empty, c->nbr, c->smask, c->tflags, c->ntype,
-                    c->f[0],     c->f[1],      c->gfield, c->partials, c->d_out};
+    void* bufs[] = {c->tile_map, c->non_empty, c->nbr,      c->smask,    c->tflags, c->ntype,
+                    c->nword,    c->f[0],      c->f[1],     c->gfield,   c->partials, c->d_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
     c->tile_map = nullptr;
@@ -73,6 +73,7 @@ void free_all(lbm_ctx* c) {
     c->smask = nullptr;
     c->tflags = nullptr;
     c->ntype = nullptr;
+    c->nword = nullptr;
     c->f[0] = c->f[1] = nullptr;
     c->gfield = nullptr;
     c->partials = nullptr;
@@ -221,7 +222,8 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     c->n_tiles = count;
     const size_t copy_bytes = (size_t)count * lbm::Q * lbm::SLOTS * lbm::dtype_size(dtype);
     c->n_partials = lbm::reduce_blocks(count);
-    LBM_CREATE_CUDA(dev_alloc(&c->nbr, (size_t)count * lbm::NBR));
+    LBM_CREATE_CUDA(dev_alloc(&c->nbr, (size_t)count * lbm::NBR_STRIDE));
+    LBM_CREATE_CUDA(dev_alloc(&c->nword, (size_t)count * lbm::SLOTS));
     LBM_CREATE_CUDA(dev_alloc(&c->smask, (size_t)count));
     LBM_CREATE_CUDA(dev_alloc(&c->tflags, (size_t)count));
     LBM_CREATE_CUDA(dev_alloc(&c->ntype, (size_t)count * lbm::SLOTS));
@@ -234,7 +236,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     LBM_CREATE_CUDA(cudaMemcpyAsync(&nonsolid, c->d_out, sizeof(nonsolid), cudaMemcpyDeviceToHost, c->stream));
     LBM_CREATE_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), c->stream));
     if (count > 0) {
-        k_check_nbr<<<152 * 4, 256, 0, c->stream>>>(c->nbr, count * lbm::NBR, count, d_bad);
+        k_check_nbr<<<152 * 4, 256, 0, c->stream>>>(c->nbr, count * lbm::NBR_STRIDE, count, d_bad);
         LBM_CREATE_CUDA(cudaGetLastError());
     }
     LBM_CREATE_CUDA(cudaMemcpyAsync(&bad, d_bad, sizeof(bad), cudaMemcpyDeviceToHost, c->stream));
@@ -243,6 +245,9 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
         fail(c, LBM_EINTERNAL, "neighbour table holds an out-of-range tile rank");
         return bail(LBM_EINTERNAL);
     }
+    // only after the check above: this kernel dereferences the neighbour ranks
+    LBM_CREATE_CUDA(lbm::launch_node_words(c));
+    LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
     c->n_nonsolid = (int64_t)nonsolid;
     c->p.omega = 1.0;
     c->p.beta = 0.5;

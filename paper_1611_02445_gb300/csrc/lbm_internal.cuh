@@ -3,9 +3,13 @@
 // Device data layout (all in HBM, allocated once per context):
 //   tile_map [Tz*Ty*Tx]  int32   rank of a kept tile, or -1 (Sec. 3.1 tileMap)
 //   non_empty[n_tiles]   uint32  linear tile index t = tx + Tx (ty + Ty tz) (nonEmptyTiles)
-//   nbr      [n_tiles][27] int32 ranks of the 3x3x3 tile neighbourhood, index
+//   nbr      [n_tiles][28] int32 ranks of the 3x3x3 tile neighbourhood, index
 //                               13 + dx + 3 dy + 9 dz, -1 for dropped or out-of-box tiles
-//                               (the local tileMap copy of Sec. 3.4, precomputed once)
+//                               (the local tileMap copy of Sec. 3.4, precomputed once);
+//                               entry 27 is padding so each record is 112 bytes
+//   nword    [n_tiles][64] uint32 per node: bit i (1..18) set when the gather of
+//                               direction i bounces back (source solid, dropped or
+//                               outside the box); bits 20-21 the node type
 //   smask    [n_tiles]   uint64  bit s set when node s of the tile is solid or padding
 //   tflags   [n_tiles]   uint32  bit 0: the tile holds inlet or outlet nodes
 //   ntype    [n_tiles][64] uint8 node types in slot order (the per-tile nodeType block)
@@ -29,6 +33,8 @@ constexpr int Q = 19;
 constexpr int TILE = 4;
 constexpr int SLOTS = 64;
 constexpr int NBR = 27;
+constexpr int NBR_STRIDE = 28;   // padded neighbour record: 112 bytes, 16-byte aligned
+constexpr int WORD_TYPE_SHIFT = 20;
 constexpr int FLAG_HAS_BC = 1;
 // F16S storage scale: h is stored as half(h * 2^12), so |h| in [1.5e-8, 16] is normal.
 constexpr float F16_SCALE = 4096.0f;
@@ -102,6 +108,7 @@ struct lbm_ctx {
     uint64_t* smask = nullptr;
     uint32_t* tflags = nullptr;
     uint8_t* ntype = nullptr;
+    uint32_t* nword = nullptr;
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
     void* gfield = nullptr;
@@ -127,6 +134,7 @@ cudaError_t launch_scan_flags(const uint8_t* flag, int64_t n, int32_t* tile_map,
                               int64_t* d_count, int64_t* block_sums, int64_t nblocks, cudaStream_t st);
 int64_t scan_block_count(int64_t n);
 cudaError_t launch_tile_meta(lbm_ctx* c, const uint8_t* nt);
+cudaError_t launch_node_words(lbm_ctx* c);
 cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]);
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B);
 cudaError_t launch_reduce(lbm_ctx* c, double* d_out);

@@ -1,19 +1,21 @@
 // lbm_step.cu -- the fused collide-and-stream step kernel (Sec. 3.4, Algorithm 2).
 //
-// One CTA of 128 threads handles two kept tiles; thread s of a tile owns slot s
-// (node x + 4 y + 16 z of the tile). Per CTA:
-//   1. stage the 3x3x3 neighbourhood of each tile (tile ranks -> element offsets of the
-//      tile's data blocks) and the neighbours' 64-bit solid masks in shared memory
-//      (the local tileMap / nodeType copies of Algorithm 2, as bit masks), one barrier;
-//   2. every non-solid node pulls f_i from x - c_i: from its own tile or a neighbour
-//      tile's data block i; a solid, dropped or out-of-box source gives halfway
-//      bounce-back f_i(x) <- A_inv(i)(x) (Sec. 2.2 walls; propagation only between
-//      non-solid nodes, Sec. 3.4);
-//   3. moments, boundary closures (inlet / outlet) or LBGK + Guo collision (Eq. 2, 3, 7);
-//   4. store all 19 populations to the other copy, coalesced (64 consecutive slots of a
-//      data block per warp pair).
-// Solid nodes issue no loads and no stores. All 19 gathers of a thread are independent
-// loads, so each thread keeps 19 requests in flight.
+// Work unit: a group of GROUP_TILES = 4 kept tiles, one thread per slot (256 threads;
+// thread s of a tile owns node x + 4 y + 16 z). Persistent CTAs walk the groups
+// b, b + G, b + 2G, ... with a software pipeline, so that while a group is computed the
+// next group's gathers are already in flight:
+//   meta(g)   cp.async of the group's neighbour records (the local tileMap copy of
+//             Algorithm 2, 28 ranks per tile) and per-node gather words (which
+//             directions bounce, node type) into a 3-slot shared-memory ring;
+//   gather(g) every non-solid node pulls f_i from x - c_i -- its own tile's or a
+//             neighbour tile's data block i -- or, when the word says the source is
+//             solid, dropped or outside the box, its own A_inv(i)(x) (halfway
+//             bounce-back, Sec. 2.2; propagation only between non-solid nodes,
+//             Sec. 3.4): 19 cp.async copies per node into a 2-slot staging ring, so
+//             the bytes in flight do not occupy registers;
+//   compute(g) moments, inlet/outlet closures or LBGK + Guo collision (Eq. 2, 3, 7)
+//             and coalesced stores of all 19 results into the other copy.
+// Solid nodes issue no copies and no stores.
 #include <algorithm>
 
 #include "lbm_internal.cuh"
@@ -21,8 +23,10 @@
 
 namespace lbm {
 
-constexpr int STEP_TILES = 2;
-constexpr int STEP_THREADS = STEP_TILES * SLOTS;
+constexpr int GROUP_TILES = 4;
+constexpr int STEP_THREADS = GROUP_TILES * SLOTS;   // 256
+constexpr int META_SLOTS = 3;
+constexpr int DATA_SLOTS = 2;
 
 // LBGK + Guo update of one direction pair (i, inv(i)) with lattice velocity c = c_i.
 // Works on f (SHIFT = false, D = rho) or on h = f - w (SHIFT = true, D = rho - 1):
@@ -112,67 +116,202 @@ __device__ __forceinline__ void collide(R v[Q], int type, const StepParams& p, R
     }
 }
 
-template <int DT>
-__global__ void __launch_bounds__(STEP_THREADS)
-k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
-       const int32_t* __restrict__ nbr, const uint64_t* __restrict__ smask,
-       const uint32_t* __restrict__ tflags, const uint8_t* __restrict__ ntype, int64_t n_tiles,
-       StepParams p) {
-    using R = typename Store<DT>::R;
-    __shared__ int64_t s_base[STEP_TILES][NBR];   // element offset of a neighbour's block 0, -1 if absent
-    __shared__ uint64_t s_mask[STEP_TILES][NBR];
-    __shared__ uint32_t s_flag[STEP_TILES];
-    const int lt = threadIdx.x >> 6;
-    const int s = threadIdx.x & 63;
-    const int64_t k = (int64_t)blockIdx.x * STEP_TILES + lt;
-    if (s < NBR) {
-        const int64_t nk = k < n_tiles ? (int64_t)nbr[k * NBR + s] : -1;
-        s_base[lt][s] = nk >= 0 ? nk * (Q * SLOTS) : -1;
-        s_mask[lt][s] = nk >= 0 ? smask[nk] : ~0ull;
-    } else if (s == 32) {
-        s_flag[lt] = k < n_tiles ? tflags[k] : 0u;
-    }
-    __syncthreads();
-    if (k >= n_tiles) return;
-    if ((s_mask[lt][13] >> s) & 1) return;   // solid node: no load, no store
+// ---------------------------------------------------------------------------- cp.async
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// Staged element: the stored element for F64/F32; for F16S the aligned 32-bit word that
+// holds the wanted half (cp.async moves at least 4 bytes), with the half picked later.
+template <int DT> struct Staged { using E = uint32_t; };
+template <> struct Staged<LBM_F64> { using E = uint64_t; };
+
+template <int DT>
+struct StepSmem {
+    using E = typename Staged<DT>::E;
+    using G = typename Store<DT>::R;
+    int32_t nbr[META_SLOTS][GROUP_TILES][NBR_STRIDE];
+    uint32_t word[META_SLOTS][STEP_THREADS];
+    G gf[META_SLOTS][STEP_THREADS];
+    E data[DATA_SLOTS][Q][STEP_THREADS];
+};
+
+template <int DT>
+__device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int slot, int64_t grp, int64_t n_tiles,
+                                           const int32_t* __restrict__ nbr, const uint32_t* __restrict__ nword,
+                                           const void* gfield) {
+    const int t = threadIdx.x;
+    const int64_t k0 = grp * GROUP_TILES;
+    // neighbour records: GROUP_TILES x 112 bytes = 28 chunks of 16 bytes
+    if (t < GROUP_TILES * (NBR_STRIDE / 4)) {
+        const int lt = t / (NBR_STRIDE / 4), c = t % (NBR_STRIDE / 4);
+        if (k0 + lt < n_tiles) cp_async16(&sm.nbr[slot][lt][4 * c], nbr + (k0 + lt) * NBR_STRIDE + 4 * c);
+    }
+    const int64_t k = k0 + (t >> 6);
+    if (k < n_tiles) {
+        cp_async4(&sm.word[slot][t], nword + k * SLOTS + (t & 63));
+        if (gfield) {
+            const typename Store<DT>::R* g = static_cast<const typename Store<DT>::R*>(gfield);
+            if (DT == LBM_F64) cp_async8(&sm.gf[slot][t], g + k * SLOTS + (t & 63));
+            else cp_async4(&sm.gf[slot][t], g + k * SLOTS + (t & 63));
+        }
+    } else {
+        sm.word[slot][t] = 0;   // past the last tile: treated as solid
+    }
+}
+
+// Issue the 19 gathers of this thread's node of group grp. Returns, for F16S, the mask
+// of directions whose half is the upper half of the staged word.
+template <int DT>
+__device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, int dslot, int64_t grp,
+                                                 const typename Store<DT>::T* __restrict__ A) {
+    using T = typename Store<DT>::T;
+    const int t = threadIdx.x, lt = t >> 6, s = t & 63;
+    const uint32_t w = sm.word[mslot][t];
+    uint32_t odd = 0;
+    if ((w >> WORD_TYPE_SHIFT) == LBM_SOLID) return 0;
     const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
-    const int64_t own = k * (Q * SLOTS);
+    const int64_t own = (grp * GROUP_TILES + lt) * (Q * SLOTS);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        int64_t src;
+        if ((w >> i) & 1) {
+            src = own + inv(i) * SLOTS + s;
+        } else {
+            const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
+            const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
+            const int ss = (sx & 3) | ((sy & 3) << 2) | ((sz & 3) << 4);
+            src = (int64_t)sm.nbr[mslot][lt][nb] * (Q * SLOTS) + i * SLOTS + ss;
+        }
+        if (DT == LBM_F64) {
+            cp_async8(&sm.data[dslot][i][t], A + src);
+        } else if (DT == LBM_F32) {
+            cp_async4(&sm.data[dslot][i][t], A + src);
+        } else {
+            odd |= (uint32_t)(src & 1) << i;
+            cp_async4(&sm.data[dslot][i][t], reinterpret_cast<const char*>(A) + (src & ~(int64_t)1) * sizeof(T));
+        }
+    }
+    return odd;
+}
+
+template <int DT>
+__device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, int64_t grp, uint32_t odd,
+                                              typename Store<DT>::T* __restrict__ B, const StepParams& p) {
+    using R = typename Store<DT>::R;
+    using T = typename Store<DT>::T;
+    const int t = threadIdx.x, lt = t >> 6, s = t & 63;
+    const uint32_t w = sm.word[mslot][t];
+    const int type = (int)(w >> WORD_TYPE_SHIFT);
+    if (type == LBM_SOLID) return;
     R v[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);   // in [-1, 4]
-        const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
-        const int ss = (sx & 3) | ((sy & 3) << 2) | ((sz & 3) << 4);
-        const int64_t base = s_base[lt][nb];
-        const bool bounce = base < 0 || ((s_mask[lt][nb] >> ss) & 1);
-        const int64_t src = bounce ? own + inv(i) * SLOTS + s : base + i * SLOTS + ss;
-        v[i] = to_arith<DT>(A[src], i);
+        T e;
+        if (DT == LBM_F16S) {
+            const uint32_t word = (uint32_t)sm.data[dslot][i][t];
+            const unsigned short hbits = (unsigned short)(((odd >> i) & 1) ? (word >> 16) : (word & 0xffffu));
+            e = *reinterpret_cast<const T*>(&hbits);
+        } else {
+            const typename Staged<DT>::E raw = sm.data[dslot][i][t];
+            e = *reinterpret_cast<const T*>(&raw);
+        }
+        v[i] = to_arith<DT>(e, i);
     }
-    const int type = (s_flag[lt] & FLAG_HAS_BC) ? (int)ntype[k * SLOTS + s] : LBM_FLUID;
-    const R Fx = p.gfield ? (R)gfield_at<DT>(p.gfield, k * SLOTS + s) : R(p.g[0]);
+    const R Fx = p.gfield ? sm.gf[mslot][t] : R(p.g[0]);
     collide<R, Store<DT>::SHIFT>(v, type, p, Fx, R(p.g[1]), R(p.g[2]));
+    const int64_t own = (grp * GROUP_TILES + lt) * (Q * SLOTS);
 #pragma unroll
     for (int i = 0; i < Q; i++) B[own + i * SLOTS + s] = to_store<DT>(v[i], i);
 }
 
+// Resident CTAs per SM the kernel is compiled for: shared memory allows 4 CTAs of the
+// 4-byte formats (46 KB each) and 2 of FP64 (88 KB each); registers are capped to match.
+template <int DT> struct StepOcc { static constexpr int CTAS = 4; };
+template <> struct StepOcc<LBM_F64> { static constexpr int CTAS = 2; };
+
+template <int DT>
+__global__ void __launch_bounds__(STEP_THREADS, StepOcc<DT>::CTAS)
+k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
+       const int32_t* __restrict__ nbr, const uint32_t* __restrict__ nword, int64_t n_tiles,
+       int64_t n_groups, StepParams p) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    StepSmem<DT>& sm = *reinterpret_cast<StepSmem<DT>*>(smem_raw);
+    const int64_t G = gridDim.x;
+    const int64_t g0 = blockIdx.x;
+    if (g0 >= n_groups) return;
+    // prologue: meta(g0), meta(g0 + G), then gather(g0)
+    issue_meta<DT>(sm, 0, g0, n_tiles, nbr, nword, p.gfield);
+    cp_async_commit();
+    if (g0 + G < n_groups) issue_meta<DT>(sm, 1, g0 + G, n_tiles, nbr, nword, p.gfield);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    uint32_t odd_cur = issue_gather<DT>(sm, 0, 0, g0, A);
+    cp_async_commit();
+    int it = 0;
+    for (int64_t g = g0; g < n_groups; g += G, it++) {
+        const int m_cur = it % META_SLOTS, m_next = (it + 1) % META_SLOTS, m_next2 = (it + 2) % META_SLOTS;
+        const int d_cur = it & 1, d_next = (it + 1) & 1;
+        // pending: meta(g + G), gather(g)
+        cp_async_wait<1>();
+        __syncthreads();   // meta(g + G) visible; everyone done with iteration it - 1
+        if (g + 2 * G < n_groups) issue_meta<DT>(sm, m_next2, g + 2 * G, n_tiles, nbr, nword, p.gfield);
+        cp_async_commit();
+        uint32_t odd_next = 0;
+        if (g + G < n_groups) odd_next = issue_gather<DT>(sm, m_next, d_next, g + G, A);
+        cp_async_commit();
+        // pending: gather(g), meta(g + 2G), gather(g + G)
+        cp_async_wait<2>();
+        compute_store<DT>(sm, m_cur, d_cur, g, odd_cur, B, p);
+        odd_cur = odd_next;
+    }
+    cp_async_wait<0>();
+}
+
+template <int DT>
+static int step_grid(int64_t n_groups) {
+    static int per_sm = -1, n_sm = 0;
+    if (per_sm < 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaFuncSetAttribute(k_step<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StepSmem<DT>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT>, STEP_THREADS, sizeof(StepSmem<DT>));
+        if (per_sm < 1) per_sm = 1;
+    }
+    return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)per_sm * n_sm));
+}
+
+template <int DT>
+static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
+    using T = typename Store<DT>::T;
+    const int64_t n_groups = (c->n_tiles + GROUP_TILES - 1) / GROUP_TILES;
+    const int grid = step_grid<DT>(n_groups);
+    k_step<DT><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
+        (const T*)A, (T*)B, c->nbr, c->nword, c->n_tiles, n_groups, c->p);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B) {
     if (c->n_tiles == 0) return cudaSuccess;
-    const int64_t blocks = (c->n_tiles + STEP_TILES - 1) / STEP_TILES;
     switch (c->dtype) {
-        case LBM_F64:
-            k_step<LBM_F64><<<(unsigned)blocks, STEP_THREADS, 0, c->stream>>>(
-                (const double*)A, (double*)B, c->nbr, c->smask, c->tflags, c->ntype, c->n_tiles, c->p);
-            break;
-        case LBM_F32:
-            k_step<LBM_F32><<<(unsigned)blocks, STEP_THREADS, 0, c->stream>>>(
-                (const float*)A, (float*)B, c->nbr, c->smask, c->tflags, c->ntype, c->n_tiles, c->p);
-            break;
-        default:
-            k_step<LBM_F16S><<<(unsigned)blocks, STEP_THREADS, 0, c->stream>>>(
-                (const __half*)A, (__half*)B, c->nbr, c->smask, c->tflags, c->ntype, c->n_tiles, c->p);
+        case LBM_F64: return launch_step_dt<LBM_F64>(c, A, B);
+        case LBM_F32: return launch_step_dt<LBM_F32>(c, A, B);
+        default: return launch_step_dt<LBM_F16S>(c, A, B);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace lbm

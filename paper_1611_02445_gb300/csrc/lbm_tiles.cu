@@ -171,7 +171,9 @@ __global__ void __launch_bounds__(64) k_tile_meta(const uint8_t* __restrict__ nt
                     else inside = false;
                 }
             }
-            nbr[k * NBR + s] = inside ? tile_map[c[0] + (int64_t)Tx * (c[1] + (int64_t)Ty * c[2])] : -1;
+            nbr[k * NBR_STRIDE + s] = inside ? tile_map[c[0] + (int64_t)Tx * (c[1] + (int64_t)Ty * c[2])] : -1;
+        } else if (s == NBR) {
+            nbr[k * NBR_STRIDE + s] = -1;
         }
         __syncthreads();
         if (s == 0) {
@@ -192,6 +194,41 @@ cudaError_t launch_tile_meta(lbm_ctx* c, const uint8_t* nt) {
                                                             c->periodic, c->tile_map, c->non_empty,
                                                             c->n_tiles, c->nbr, c->smask, c->tflags,
                                                             c->ntype, d_cnt);
+    return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Per-node gather words: for every non-solid node, which of the 18 moving directions
+// bounce back (their source x - c_i is solid, in a dropped tile or outside a
+// non-periodic box), plus the node type. Built once; the step kernel then needs no
+// neighbour masks.
+__global__ void __launch_bounds__(64) k_node_words(const int32_t* __restrict__ nbr, const uint64_t* __restrict__ smask,
+                                                   const uint8_t* __restrict__ ntype, int64_t n_tiles,
+                                                   uint32_t* __restrict__ nword) {
+    const int s = threadIdx.x;
+    const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
+    for (int64_t k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+        const uint32_t type = ntype[k * SLOTS + s];
+        uint32_t w = 0;
+        if (type != LBM_SOLID) {
+            w = type << WORD_TYPE_SHIFT;
+#pragma unroll
+            for (int i = 1; i < Q; i++) {
+                const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
+                const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
+                const int ss = (sx & 3) | ((sy & 3) << 2) | ((sz & 3) << 4);
+                const int32_t nk = nbr[k * NBR_STRIDE + nb];
+                const bool bounce = nk < 0 || ((smask[nk] >> ss) & 1);
+                if (bounce) w |= 1u << i;
+            }
+        }
+        nword[k * SLOTS + s] = w;
+    }
+}
+
+cudaError_t launch_node_words(lbm_ctx* c) {
+    const int64_t blocks = std::min<int64_t>(c->n_tiles, 1 << 20);
+    if (blocks > 0) k_node_words<<<(unsigned)blocks, 64, 0, c->stream>>>(c->nbr, c->smask, c->ntype, c->n_tiles, c->nword);
     return cudaGetLastError();
 }
 
