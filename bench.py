@@ -155,6 +155,57 @@ def run_reference(args, nt, tau, g):
             "e2e": {"value": value, "unit": "MFLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_adjoint_workload(args):
+    """Adjoint workload: 128^3 sphere pack (radius 8, porosity 0.4, seed 161102448), FP32
+    storage, tau 0.8, per-node x force 1e-5 + N(0, 1e-7) (seed 161102449), periodic;
+    L = mean u_x over the plane x = 127 after T = 2000 steps from rest; checkpoints every
+    100 steps. Reports the time of the forward alone and of forward + reverse sweep, and
+    checks dL/dtau and one directional dL/dg against central differences (relative step
+    1e-3) of the FP64 forward and against the FP64 adjoint."""
+    import torch
+    import __graft_entry__
+    from paper_1611_02445_gb300 import inputs as I
+    from paper_1611_02445_gb300 import lbm
+    __graft_entry__.build()
+    nt = I.sphere_pack(128, 8.0, 0.4, I.SEED_POROUS_128)
+    gf = I.body_force_field(nt, 1e-5, 1e-7, I.SEED_FORCE_NOISE)
+    T, K, plane, tau = args.adj_steps, 100, 127, 0.8
+
+    def run(dtype, tau_, gf_, grads):
+        with lbm.Lattice(nt, dtype, 0b111) as L:
+            L.set_params(tau_, (0.0, 0.0, 0.0), gf_)
+            L.init_equilibrium()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = L.adjoint(T, K, plane, grads)
+            torch.cuda.synchronize()
+            return out, time.perf_counter() - t0, L.info()
+
+    run("f32", tau, gf, False)                      # warm-up
+    (L32f, _, _), t_fwd, info = run("f32", tau, gf, False)
+    (L32, dg32, dtau32), t_adj, _ = run("f32", tau, gf, True)
+    (L64, dg64, dtau64), t_adj64, _ = run("f64", tau, gf, True)
+    e = 1e-3
+    fd_tau = (run("f64", tau * (1 + e), gf, False)[0][0] - run("f64", tau * (1 - e), gf, False)[0][0]) / (2 * e * tau)
+    d = np.random.default_rng(0).standard_normal(nt.shape) * gf
+    fd_g = (run("f64", tau, gf + e * d, False)[0][0] - run("f64", tau, gf - e * d, False)[0][0]) / (2 * e)
+    m = nt != 0
+    line = {"workload": "adjoint: sphere pack 128^3, porosity 0.4, FP32 storage, tau 0.8, g = 1e-5 + N(0,1e-7), "
+                        f"L = mean u_x on x = 127 after T = {T}, checkpoints every {K}",
+            "n_nonsolid": info["n_nonsolid"], "n_tiles": info["n_tiles"],
+            "forward_s": t_fwd, "forward_plus_adjoint_s": t_adj, "ratio": t_adj / t_fwd,
+            "f64_forward_plus_adjoint_s": t_adj64,
+            "loss_f32": L32, "loss_f64": L64,
+            "dL_dtau": {"f32_adjoint": dtau32, "f64_adjoint": dtau64, "f64_central_fd": fd_tau,
+                        "rel_err_f64_vs_fd": abs(dtau64 - fd_tau) / abs(fd_tau),
+                        "rel_err_f32_vs_f64": abs(dtau32 - dtau64) / abs(dtau64)},
+            "dL_dg_directional": {"f64_adjoint": float((dg64 * d).sum()), "f32_adjoint": float((dg32 * d).sum()),
+                                  "f64_central_fd": fd_g,
+                                  "rel_err_f64_vs_fd": abs(float((dg64 * d).sum()) - fd_g) / abs(fd_g)},
+            "dL_dg_f32_vs_f64_max_rel": float(np.abs(dg32[m] - dg64[m]).max() / np.abs(dg64).max())}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -164,11 +215,16 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16s"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--adjoint", action="store_true", help="run the adjoint workload instead")
+    ap.add_argument("--adj-steps", type=int, default=2000)
     ap.add_argument("--size", type=int, default=256,
                     help="edge of the cubic sphere pack (256 is the benchmark workload; smaller "
                          "sizes are for profiling captures)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    if args.adjoint:
+        run_adjoint_workload(args)
+        return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

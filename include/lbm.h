@@ -127,6 +127,26 @@ lbm_status lbm_get_f_box(lbm_ctx* ctx, int x0, int y0, int z0, int bx, int by, i
 lbm_status lbm_get_f(lbm_ctx* ctx, double* f_dense);
 lbm_status lbm_set_f(lbm_ctx* ctx, const double* f_dense);
 
+/* Gradient of an outlet-flux loss by a hand-written discrete adjoint of the step (the
+ * paper has no adjoint; the forward map is the step of Sec. 3.4 / Eq. 7). From the
+ * current state s_0: T steps forward (the context ends in s_T, as after lbm_step(T)),
+ *   L = mean over non-solid nodes of the plane x = plane_x of u_x(s_T),
+ *       u_x = (sum_i c_ix f*_i - F_x/2) / rho,
+ * and, if dL_dg or dL_dtau is not NULL, the reverse sweep: a checkpoint is kept every
+ * ckpt_every steps, each segment is recomputed from its checkpoint and T adjoint-step
+ * kernels run backwards.
+ *   loss      host, receives L (0 if the plane has no non-solid node).
+ *   dL_dg     nx*ny*nz doubles, dense: dL/dF_x per node, F_x being the per-node x force
+ *             (the field of lbm_set_params, or g[0] everywhere); 0 at solid nodes.
+ *             Device pointer if dL_dg_on_device, else host. May be NULL.
+ *   dL_dtau   host, receives dL/dtau. May be NULL.
+ * Gradients accumulate in FP64; the adjoint arithmetic runs in the storage's arithmetic
+ * precision (FP64 for LBM_F64, FP32 otherwise). Device memory: (ceil(T/ckpt_every) +
+ * min(ckpt_every, T)) population copies plus two adjoint copies; if it cannot be
+ * allocated the call returns LBM_ENOMEM before any work and the state is unchanged. */
+lbm_status lbm_adjoint(lbm_ctx* ctx, int T, int ckpt_every, int plane_x, double* loss, double* dL_dg,
+                       int dL_dg_on_device, double* dL_dtau);
+
 /* Tile structures (Sec. 3.1): tile_map has ceil(nx/4)*ceil(ny/4)*ceil(nz/4) int32 entries
  * (rank of the tile among the kept tiles, or -1), non_empty has *n_tiles uint32 linear tile
  * indices t = tx + Tx (ty + Ty tz) in discovery order. Either array may be NULL. Host. */

@@ -410,6 +410,27 @@ lbm_status lbm_set_f(lbm_ctx* c, const double* f_dense) {
     return LBM_OK;
 }
 
+lbm_status lbm_adjoint(lbm_ctx* c, int T, int ckpt_every, int plane_x, double* loss, double* dL_dg,
+                       int dL_dg_on_device, double* dL_dtau) {
+    LBM_CHECK_CTX(c);
+    if (T < 1 || ckpt_every < 1 || !loss) return fail(c, LBM_EINVAL, "T >= 1, ckpt_every >= 1 and loss are required");
+    if (plane_x < 0 || plane_x >= c->nx) return fail(c, LBM_EINVAL, "plane_x outside the box");
+    if (!c->state_set || !c->params_set) return fail(c, LBM_ESTATE, "set parameters and a state first");
+    if (c->n_tiles == 0) {
+        *loss = 0.0;
+        if (dL_dtau) *dL_dtau = 0.0;
+        return LBM_OK;
+    }
+    bool started = false;
+    cudaError_t e = lbm::launch_adjoint(c, T, ckpt_every, plane_x, loss, dL_dg, dL_dg_on_device, dL_dtau, &started);
+    if (e == cudaErrorMemoryAllocation && !started) {
+        c->err = "lbm_adjoint: not enough device memory for the checkpoints; state unchanged";
+        return LBM_ENOMEM;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, "lbm_adjoint", e);
+    return LBM_OK;
+}
+
 lbm_status lbm_get_tiles(lbm_ctx* c, int32_t* tile_map, uint32_t* non_empty, int64_t* n_tiles) {
     LBM_CHECK_CTX(c);
     if (n_tiles) *n_tiles = c->n_tiles;

@@ -142,4 +142,6 @@ cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64);
 cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* d_out);
 cudaError_t launch_set_dense(lbm_ctx* c, const double* d_dense);
 cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense);
+cudaError_t launch_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, double* dL_dg, int dg_on_device,
+                           double* dL_dtau, bool* started);
 }  // namespace lbm

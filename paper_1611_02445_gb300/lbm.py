@@ -68,6 +68,7 @@ def load():
     L.lbm_get_info.argtypes = [vp, ct.POINTER(i64), ct.POINTER(i64), ct.POINTER(i64)]
     L.lbm_save_state.argtypes = [vp, vp, ct.POINTER(ct.c_size_t)]
     L.lbm_load_state.argtypes = [vp, vp, ct.c_size_t]
+    L.lbm_adjoint.argtypes = [vp, i, i, i, pd, vp, i, pd]
     L.lbm_build_tiles_noalloc.argtypes = [vp, i, i, i, vp, vp, ct.POINTER(i64), vp]
     for name in header_functions():
         getattr(L, name)   # every declared entry point must be exported
@@ -222,6 +223,19 @@ def lbm_load_state(ctx, blob: bytes):
     _check(load().lbm_load_state(ctx, blob, len(blob)), ctx)
 
 
+def lbm_adjoint(ctx, T, ckpt_every, plane_x, dL_dg=None, want_dtau=True):
+    """Outlet-flux loss after T steps and, when dL_dg (a host numpy array or a device
+    tensor of nx*ny*nz doubles) or want_dtau is given, its gradients. Returns
+    (L, dL/dtau or None)."""
+    loss = ct.c_double()
+    dtau = ct.c_double()
+    if isinstance(dL_dg, np.ndarray):
+        assert dL_dg.dtype == np.float64 and dL_dg.flags.c_contiguous
+    _check(load().lbm_adjoint(ctx, int(T), int(ckpt_every), int(plane_x), ct.byref(loss), _ptr(dL_dg),
+                              _on_device(dL_dg), ct.byref(dtau) if want_dtau else None), ctx)
+    return loss.value, (dtau.value if want_dtau else None)
+
+
 NOALLOC_MAX_TILES = 1 << 22
 
 
@@ -311,6 +325,12 @@ class Lattice:
         n_tiles, n_nonsolid, copy_bytes = lbm_get_info(self.ctx)
         return {"n_tiles": n_tiles, "n_nonsolid": n_nonsolid, "copy_bytes": copy_bytes,
                 "eta_t": n_nonsolid / (64 * n_tiles) if n_tiles else 0.0}
+
+    def adjoint(self, T, ckpt_every, plane_x, grads=True):
+        """(L, dL/dF_x dense numpy array or None, dL/dtau or None) after T steps."""
+        dg = np.zeros(self.shape, np.float64) if grads else None
+        L, dtau = lbm_adjoint(self.ctx, T, ckpt_every, plane_x, dg, grads)
+        return L, dg, dtau
 
     def save_state(self) -> bytes:
         return lbm_save_state(self.ctx)

@@ -1,0 +1,146 @@
+"""GPU adjoint (lbm_adjoint, through the C ABI) against the oracle adjoint and against
+central finite differences of the GPU's own FP64 forward.
+
+Bars: FP64 storage -- loss to 1e-12 relative, gradients to 1e-10 of their largest
+entry (the kernels reorder sums and contract multiply-adds); checkpoint spacing
+changes nothing (the recompute is deterministic); finite differences with a relative
+step of 1e-3 agree to 1e-4 relative. FP32 storage -- the error against the FP64
+oracle adjoint is stated and bounded.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1611_02445_gb300 import build as B
+from paper_1611_02445_gb300 import inputs as I
+from paper_1611_02445_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+KW = dict(u_in=(0.04, 0.01, 0.0), rho_out=1.01)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.build()
+    lbm.load()
+
+
+def gpu_adjoint(nt, f0, T, K, plane, periodic, tau, g=(0, 0, 0), gf=None, u_in=(0, 0, 0), rho_out=1.0,
+                dtype="f64", grads=True):
+    with lbm.Lattice(nt, dtype, periodic) as L:
+        L.set_params(tau, g, gf, u_in, rho_out)
+        if f0 is None:
+            L.init_equilibrium()
+        else:
+            L.set_f(f0)
+        return L.adjoint(T, K, plane, grads)
+
+
+@pytest.mark.parametrize("periodic,boundary", [(0b111, False), (0b000, True), (0b011, True)])
+def test_adjoint_f64_matches_oracle(periodic, boundary):
+    nt = I.random_box(8, 8, 12, p_solid=0.25, seed=periodic + 3, boundary=boundary)
+    rng = np.random.default_rng(periodic)
+    gf = 1e-3 * (1 + 0.1 * rng.standard_normal(nt.shape))
+    f0 = I.random_populations(nt, 0.05, seed=periodic + 9)
+    T, K, plane, tau = 7, 3, 7, 0.8
+    g = (0.0, 1e-4, -2e-4)
+    Lg, dg, dtau = gpu_adjoint(nt, f0, T, K, plane, periodic, tau, g, gf, **KW)
+    Lo, dg_o, _, dtau_o = O.adjoint(nt, T, plane, periodic, tau, g, gf, f0=f0, **KW)
+    assert abs(Lg - Lo) <= 1e-12 * max(abs(Lo), 1e-30)
+    m = nt != 0
+    assert np.abs(dg[m] - dg_o[m]).max() <= 1e-10 * np.abs(dg_o).max()
+    assert (dg[~m] == 0).all()
+    assert abs(dtau - dtau_o) <= 1e-10 * abs(dtau_o)
+
+
+def test_adjoint_checkpoint_spacing_changes_nothing():
+    nt = I.random_box(12, 8, 8, p_solid=0.3, seed=21)
+    f0 = I.random_populations(nt, 0.05, seed=22)
+    gf = np.full(nt.shape, 2e-4)
+    ref = None
+    for K in (1, 4, 10, 50):
+        out = gpu_adjoint(nt, f0, 10, K, 11, 0b111, 0.75, gf=gf)
+        if ref is None:
+            ref = out
+        else:
+            assert out[0] == ref[0] and out[2] == ref[2]
+            assert np.array_equal(out[1], ref[1])
+
+
+def test_adjoint_loss_only_and_state_after():
+    nt = I.random_box(8, 8, 8, p_solid=0.2, seed=5)
+    with lbm.Lattice(nt, "f64", 0b111) as L:
+        L.set_params(0.8, (1e-4, 0, 0))
+        L.init_equilibrium()
+        Lonly, dg, dtau = L.adjoint(5, 2, 3, grads=False)
+        f_after = L.get_f()
+        assert dg is None and dtau is None
+    with lbm.Lattice(nt, "f64", 0b111) as L:
+        L.set_params(0.8, (1e-4, 0, 0))
+        L.init_equilibrium()
+        L.step(5)
+        assert np.array_equal(L.get_f(), f_after, equal_nan=True)
+    fo = O.run(O.init(nt), nt, 5, 0b111, 0.8, (1e-4, 0, 0))
+    assert abs(Lonly - O.loss(fo, nt, 3, (1e-4, 0, 0))[0]) <= 1e-12 * abs(Lonly)
+
+
+def _crop_case():
+    """32^3 crop of the 128^3 adjoint sphere pack (porosity 0.4) with a noisy force field."""
+    nt = I.crop(I.sphere_pack(128, 8.0, 0.4, I.SEED_POROUS_128), 32)
+    gf = I.body_force_field(nt, 1e-5, 1e-7, I.SEED_FORCE_NOISE)
+    return nt, gf
+
+
+def test_adjoint_crop32_f64_and_f32_vs_oracle():
+    nt, gf = _crop_case()
+    T, K, plane, tau = 40, 16, 31, 0.8
+    Lo, dg_o, _, dtau_o = O.adjoint(nt, T, plane, 0b111, tau, g_field=gf)
+    Lg, dg, dtau = gpu_adjoint(nt, None, T, K, plane, 0b111, tau, gf=gf)
+    m = nt != 0
+    scale = np.abs(dg_o).max()
+    assert abs(Lg - Lo) <= 1e-12 * abs(Lo)
+    assert np.abs(dg[m] - dg_o[m]).max() <= 1e-10 * scale
+    assert abs(dtau - dtau_o) <= 1e-10 * abs(dtau_o)
+    L32, dg32, dtau32 = gpu_adjoint(nt, None, T, K, plane, 0b111, tau, gf=gf, dtype="f32")
+    e_L = abs(L32 - Lo) / abs(Lo)
+    e_g = np.abs(dg32[m] - dg_o[m]).max() / scale
+    e_t = abs(dtau32 - dtau_o) / abs(dtau_o)
+    print(f"f32 adjoint vs FP64 oracle: loss {e_L:.2e}, dL/dg {e_g:.2e} (of max), dL/dtau {e_t:.2e}")
+    assert e_L <= 1e-3 and e_g <= 1e-2 and e_t <= 1e-2
+
+
+def test_adjoint_f64_matches_central_differences():
+    nt, gf = _crop_case()
+    T, K, plane, tau = 60, 20, 31, 0.8
+    L0, dg, dtau = gpu_adjoint(nt, None, T, K, plane, 0b111, tau, gf=gf)
+
+    def loss(tau_, gf_):
+        return gpu_adjoint(nt, None, T, K, plane, 0b111, tau_, gf=gf_, grads=False)[0]
+
+    e = 1e-3
+    fd_tau = (loss(tau * (1 + e), gf) - loss(tau * (1 - e), gf)) / (2 * e * tau)
+    assert dtau == pytest.approx(fd_tau, rel=1e-4)
+    rng = np.random.default_rng(7)
+    for _ in range(3):
+        d = rng.standard_normal(nt.shape) * gf
+        fd = (loss(tau, gf * 1.0 + e * d) - loss(tau, gf - e * d)) / (2 * e)
+        assert float((dg * d).sum()) == pytest.approx(fd, rel=1e-4)
+
+
+def test_autograd_function_matches_c_api():
+    import torch
+    from paper_1611_02445_gb300.autograd import outlet_flux_loss
+    nt, gf = _crop_case()
+    T, K, plane = 30, 10, 31
+    g = torch.tensor(gf, dtype=torch.float64, device="cuda", requires_grad=True)
+    tau = torch.tensor(0.8, dtype=torch.float64, requires_grad=True)
+    with lbm.Lattice(nt, "f64", 0b111) as L:
+        out = outlet_flux_loss(g, tau, L, T, plane, K)
+        out.backward()
+    L0, dg, dtau = gpu_adjoint(nt, None, T, K, plane, 0b111, 0.8, gf=gf)
+    assert float(out.detach()) == L0
+    assert np.array_equal(g.grad.cpu().numpy(), dg)
+    assert float(tau.grad) == dtau
