@@ -53,9 +53,17 @@ typedef enum {
     LBM_EINTERNAL = 8      /* internal consistency check failed */
 } lbm_status;
 
-/* Storage of the populations. Arithmetic is FP64 for LBM_F64 and FP32 otherwise;
- * LBM_F16S stores h_i = (f_i - w_i) * 2^12 as IEEE binary16 (round to nearest even). */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2 } lbm_dtype;
+/* Storage of the populations and the arithmetic of the step.
+ *   LBM_F64         FP64 storage. The moment sums and the final (1 - 1/tau) f + Y update
+ *                   run in FP64; Y = f^eq/tau + S runs in double-float (pairs of FP32,
+ *                   about 46-48 bits), because GB300's FP64 pipe has 2 lanes per SM.
+ *                   Agrees with FP64 arithmetic to ~1e-14 relative per step.
+ *   LBM_F64_NATIVE  FP64 storage, every operation of the step in FP64.
+ *   LBM_F32         FP32 storage, FP32 arithmetic.
+ *   LBM_F16S        stores h_i = (f_i - w_i) * 2^12 as IEEE binary16 (round to nearest
+ *                   even), FP32 arithmetic.
+ * Inlet/outlet nodes use the FP64 arithmetic in both FP64 modes. */
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F64_NATIVE = 3 } lbm_dtype;
 
 enum { LBM_SOLID = 0, LBM_FLUID = 1, LBM_INLET = 2, LBM_OUTLET = 3 };
 enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };

@@ -155,7 +155,8 @@ __device__ __forceinline__ R collide_adjoint(const R v[Q], const R lam[Q], int t
     R rhobar = 0, ubx = 0, uby = 0, ubz = 0, Fbx = 0;
     R keep = 0;   // coefficient of lam_i kept in mu_i
     if (type == LBM_INLET) {
-        const R ex = R(p.u_in[0]), ey = R(p.u_in[1]), ez = R(p.u_in[2]);
+        const R ex = par<R>(p.u_in[0], p.u_in_f[0]), ey = par<R>(p.u_in[1], p.u_in_f[1]),
+                ez = par<R>(p.u_in[2], p.u_in_f[2]);
         const R M2ex = Mxx * ex + Mxy * ey + Mxz * ez, M2ey = Mxy * ex + Myy * ey + Myz * ez,
                 M2ez = Mxz * ex + Myz * ey + Mzz * ez;
         rhobar = M0 * (R(1) - R(1.5) * (ex * ex + ey * ey + ez * ez)) + R(3) * (M1x * ex + M1y * ey + M1z * ez) +
@@ -167,12 +168,12 @@ __device__ __forceinline__ R collide_adjoint(const R v[Q], const R lam[Q], int t
     const R M2ux = Mxx * ux + Mxy * uy + Mxz * uz, M2uy = Mxy * ux + Myy * uy + Myz * uz,
             M2uz = Mxz * ux + Myz * uy + Mzz * uz;
     if (type == LBM_OUTLET) {
-        const R ro = R(p.rho_out);
+        const R ro = par<R>(p.rho_out, p.rho_out_f);
         ubx = ro * (R(3) * M1x + R(9) * M2ux - R(3) * ux * M0);
         uby = ro * (R(3) * M1y + R(9) * M2uy - R(3) * uy * M0);
         ubz = ro * (R(3) * M1z + R(9) * M2uz - R(3) * uz * M0);
     } else {
-        const R omega = R(p.omega), beta = R(p.beta);
+        const R omega = par<R>(p.omega, p.omega_f), beta = par<R>(p.beta, p.beta_f);
         const R uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
         const R M1u = M1x * ux + M1y * uy + M1z * uz, M1F = M1x * Fx + M1y * Fy + M1z * Fz;
         const R uM2u = ux * M2ux + uy * M2uy + uz * M2uz;
@@ -245,8 +246,9 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const typename Store<DT
                 lam[inv(i)] = bounce ? mu_in[own + i * SLOTS + s] : mu_in[s_base[lt][nb] + inv(i) * SLOTS + ss];
             }
         }
-        const R Fx = gfield ? (R)gfield_at<DT>(gfield, k * SLOTS + s) : R(p.g[0]);
-        const R Fb = collide_adjoint<R, Store<DT>::SHIFT>(v, lam, type, p, Fx, R(p.g[1]), R(p.g[2]), mu, taubar);
+        const R Fx = gfield ? (R)gfield_at<DT>(gfield, k * SLOTS + s) : par<R>(p.g[0], p.g_f[0]);
+        const R Fb = collide_adjoint<R, Store<DT>::SHIFT>(v, lam, type, p, Fx, par<R>(p.g[1], p.g_f[1]),
+                                                          par<R>(p.g[2], p.g_f[2]), mu, taubar);
 #pragma unroll
         for (int i = 0; i < Q; i++) mu_out[own + i * SLOTS + s] = mu[i];
         gbar[k * SLOTS + s] += (double)Fb;

@@ -63,8 +63,9 @@ cudaError_t dev_alloc(T** p, size_t count) {
 }
 
 void free_all(lbm_ctx* c) {
-    void* bufs[] = {c->tile_map, c->non_empty, c->nbr,      c->smask,    c->tflags, c->ntype,
-                    c->nword,    c->f[0],      c->f[1],     c->gfield,   c->partials, c->d_out};
+    void* bufs[] = {c->tile_map, c->non_empty, c->nbr,    c->smask,  c->tflags, c->ntype,    c->nword,
+                    c->groups,   c->fword,     c->fidx,   c->gfield, c->gfield_c, c->f[0], c->f[1],
+                    c->partials, c->d_out};
     for (void* b : bufs)
         if (b) cudaFree(b);
     c->tile_map = nullptr;
@@ -74,6 +75,10 @@ void free_all(lbm_ctx* c) {
     c->tflags = nullptr;
     c->ntype = nullptr;
     c->nword = nullptr;
+    c->groups = nullptr;
+    c->fword = nullptr;
+    c->fidx = nullptr;
+    c->gfield_c = nullptr;
     c->f[0] = c->f[1] = nullptr;
     c->gfield = nullptr;
     c->partials = nullptr;
@@ -146,7 +151,10 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     if (!node_type) return fail(nullptr, LBM_EINVAL, "node_type is NULL");
     if (tile != lbm::TILE) return fail(nullptr, LBM_EUNSUPPORTED, "only 4x4x4 tiles are supported");
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "dimensions must be >= 1");
-    if (dtype != LBM_F64 && dtype != LBM_F32 && dtype != LBM_F16S) return fail(nullptr, LBM_EINVAL, "unknown dtype");
+    if (dtype != LBM_F64 && dtype != LBM_F32 && dtype != LBM_F16S && dtype != LBM_F64_NATIVE)
+        return fail(nullptr, LBM_EINVAL, "unknown dtype");
+    const bool native64 = dtype == LBM_F64_NATIVE;
+    if (native64) dtype = LBM_F64;
     if (periodic & ~7u) return fail(nullptr, LBM_EINVAL, "periodic mask has bits other than x, y, z");
     const int dims[3] = {nx, ny, nz};
     for (int a = 0; a < 3; a++)
@@ -162,6 +170,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     c->Tx = (int)Tx; c->Ty = (int)Ty; c->Tz = (int)Tz;
     c->periodic = periodic;
     c->dtype = dtype;
+    c->native64 = native64;
     c->stream = static_cast<cudaStream_t>(stream);
 
     uint8_t* d_nt = nullptr;
@@ -249,6 +258,57 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     LBM_CREATE_CUDA(lbm::launch_node_words(c));
     LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
     c->n_nonsolid = (int64_t)nonsolid;
+    {
+        // Work units of the step kernel: consecutive tiles, at most GROUP_MAX_TILES of
+        // them and at most GROUP_MAX_NODES non-solid nodes, so that threads map to
+        // non-solid nodes only. Built once on the host from the per-node words.
+        std::vector<uint32_t> words((size_t)count * lbm::SLOTS);
+        if (count > 0) {
+            LBM_CREATE_CUDA(cudaMemcpyAsync(words.data(), c->nword, words.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+            LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
+        }
+        std::vector<int4> groups;
+        std::vector<uint32_t> fw, fi;
+        fw.reserve((size_t)nonsolid);
+        fi.reserve((size_t)nonsolid);
+        int64_t k = 0;
+        while (k < count) {
+            int4 g;
+            g.x = (int)k;
+            g.y = 0;
+            g.z = (int)fw.size();
+            g.w = 0;
+            while (k < count && g.y < lbm::GROUP_MAX_TILES) {
+                int cnt = 0;
+                for (int sl = 0; sl < lbm::SLOTS; sl++) cnt += (words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) != 0;
+                if (g.w + cnt > lbm::GROUP_MAX_NODES) break;
+                for (int sl = 0; sl < lbm::SLOTS; sl++) {
+                    const uint32_t w = words[k * lbm::SLOTS + sl];
+                    if ((w >> lbm::WORD_TYPE_SHIFT) == 0) continue;
+                    fw.push_back(w | ((uint32_t)g.y << lbm::WORD_LT_SHIFT) | ((uint32_t)sl << lbm::WORD_SLOT_SHIFT));
+                    fi.push_back((uint32_t)(k * lbm::SLOTS + sl));
+                }
+                g.w += cnt;
+                g.y++;
+                k++;
+            }
+            groups.push_back(g);
+        }
+        if ((int64_t)fw.size() != c->n_nonsolid) {
+            fail(c, LBM_EINTERNAL, "non-solid node count mismatch while building work groups");
+            return bail(LBM_EINTERNAL);
+        }
+        c->n_groups = (int64_t)groups.size();
+        LBM_CREATE_CUDA(dev_alloc(&c->groups, groups.size()));
+        LBM_CREATE_CUDA(dev_alloc(&c->fword, fw.size()));
+        LBM_CREATE_CUDA(dev_alloc(&c->fidx, fi.size()));
+        if (!groups.empty()) {
+            LBM_CREATE_CUDA(cudaMemcpyAsync(c->groups, groups.data(), groups.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
+            LBM_CREATE_CUDA(cudaMemcpyAsync(c->fword, fw.data(), fw.size() * 4, cudaMemcpyHostToDevice, c->stream));
+            LBM_CREATE_CUDA(cudaMemcpyAsync(c->fidx, fi.data(), fi.size() * 4, cudaMemcpyHostToDevice, c->stream));
+            LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
+        }
+    }
     c->p.omega = 1.0;
     c->p.beta = 0.5;
     c->p.rho_out = 1.0;
@@ -266,8 +326,10 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
     if (!(std::isfinite(rho_out) && rho_out > 0.0)) return fail(c, LBM_EINVAL, "rho_out must be finite and > 0");
     if (g_field) {
         const int64_t N = (int64_t)c->nx * c->ny * c->nz;
-        const size_t gbytes = (size_t)std::max<int64_t>(c->n_tiles, 1) * lbm::SLOTS * (c->dtype == LBM_F64 ? 8 : 4);
+        const size_t gsize = c->dtype == LBM_F64 ? 8 : 4;
+        const size_t gbytes = (size_t)std::max<int64_t>(c->n_tiles, 1) * lbm::SLOTS * gsize;
         if (!c->gfield) LBM_CUDA(c, cudaMalloc(&c->gfield, gbytes));
+        if (!c->gfield_c) LBM_CUDA(c, cudaMalloc(&c->gfield_c, (size_t)std::max<int64_t>(c->n_nonsolid, 1) * gsize));
         const double* d_dense = g_field;
         double* tmp = nullptr;
         if (!g_field_on_device) {
@@ -280,6 +342,7 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
             d_dense = tmp;
         }
         cudaError_t e = c->n_tiles > 0 ? lbm::launch_gfield(c, d_dense) : cudaSuccess;
+        if (e == cudaSuccess && c->n_tiles > 0) e = lbm::launch_gfield_compact(c);
         if (tmp) {
             cudaError_t e2 = cudaStreamSynchronize(c->stream);
             cudaFree(tmp);
@@ -289,7 +352,9 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
     } else if (c->gfield) {
         LBM_CUDA(c, cudaStreamSynchronize(c->stream));
         cudaFree(c->gfield);
+        cudaFree(c->gfield_c);
         c->gfield = nullptr;
+        c->gfield_c = nullptr;
     }
     c->tau = tau;
     c->p.omega = 1.0 / tau;
@@ -300,6 +365,15 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
     }
     c->p.rho_out = rho_out;
     c->p.gfield = c->gfield;
+    c->p.dfc = lbm::make_df_const(c->p.omega, c->p.beta, c->p.g[1], c->p.g[2]);
+    c->p.omega_f = (float)c->p.omega;
+    c->p.beta_f = (float)c->p.beta;
+    for (int a = 0; a < 3; a++) {
+        c->p.g_f[a] = (float)c->p.g[a];
+        c->p.u_in_f[a] = (float)c->p.u_in[a];
+    }
+    c->p.rho_out_f = (float)rho_out;
+    c->p.rho_out_m1_f = (float)(rho_out - 1.0);
     c->params_set = true;
     return LBM_OK;
 }

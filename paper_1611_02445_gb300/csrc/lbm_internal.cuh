@@ -17,6 +17,12 @@
 //                               per direction per tile (Sec. 3.2, Fig. 3), slot
 //                               s = x + 4 y + 16 z inside the tile (Eq. 11 order)
 //   gfield   [n_tiles][64]       optional per-node x force (double for F64, else float)
+//   groups   [n_groups] int4     work units of the step kernel: {first tile, tiles (<= 8),
+//                               first fluid node, fluid nodes (<= 256)}, consecutive tiles
+//   fword    [n_fluid] uint32    the gather word of every non-solid node in group order,
+//                               plus bits 22-24 its tile within the group, 25-30 its slot
+//   fidx     [n_fluid] uint32    k * 64 + s of every non-solid node in the same order
+//   gfield_c [n_fluid]           the per-node force in the same order
 #pragma once
 
 #include <cuda_runtime.h>
@@ -26,6 +32,7 @@
 #include <string>
 
 #include "../../include/lbm.h"
+#include "lbm_collide_df.cuh"
 
 namespace lbm {
 
@@ -35,6 +42,10 @@ constexpr int SLOTS = 64;
 constexpr int NBR = 27;
 constexpr int NBR_STRIDE = 28;   // padded neighbour record: 112 bytes, 16-byte aligned
 constexpr int WORD_TYPE_SHIFT = 20;
+constexpr int WORD_LT_SHIFT = 22;      // compact words: tile within the group (3 bits)
+constexpr int WORD_SLOT_SHIFT = 25;    // compact words: slot in the tile (6 bits)
+constexpr int GROUP_MAX_TILES = 8;
+constexpr int GROUP_MAX_NODES = 256;
 constexpr int FLAG_HAS_BC = 1;
 // F16S storage scale: h is stored as half(h * 2^12), so |h| in [1.5e-8, 16] is normal.
 constexpr float F16_SCALE = 4096.0f;
@@ -92,14 +103,23 @@ struct StepParams {
     double u_in[3];
     double rho_out;
     const void* gfield;
+    DFConst dfc;   // constants of the double-float FP64 collision
+    // FP32 copies for the 4-byte formats (an FP64 -> FP32 conversion runs on the FP64 pipe)
+    float omega_f, beta_f, g_f[3], u_in_f[3], rho_out_f, rho_out_m1_f;
 };
+
+// A parameter in the arithmetic type R: the FP64 value or its FP32 copy.
+template <typename R> __host__ __device__ inline R par(double d, float f);
+template <> __host__ __device__ inline double par<double>(double d, float) { return d; }
+template <> __host__ __device__ inline float par<float>(double, float f) { return f; }
 
 }  // namespace lbm
 
 struct lbm_ctx {
     int nx = 0, ny = 0, nz = 0, Tx = 0, Ty = 0, Tz = 0;
     unsigned periodic = 0;
-    int dtype = LBM_F64;
+    int dtype = LBM_F64;        // storage format (LBM_F64, LBM_F32, LBM_F16S)
+    bool native64 = false;      // LBM_F64_NATIVE: FP64 arithmetic throughout
     int64_t n_tiles = 0, n_nonsolid = 0;
     cudaStream_t stream = nullptr;
     int32_t* tile_map = nullptr;
@@ -109,6 +129,11 @@ struct lbm_ctx {
     uint32_t* tflags = nullptr;
     uint8_t* ntype = nullptr;
     uint32_t* nword = nullptr;
+    int4* groups = nullptr;
+    uint32_t* fword = nullptr;
+    uint32_t* fidx = nullptr;
+    void* gfield_c = nullptr;
+    int64_t n_groups = 0;
     void* f[2] = {nullptr, nullptr};
     int cur = 0;
     void* gfield = nullptr;
@@ -142,6 +167,7 @@ cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64);
 cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* d_out);
 cudaError_t launch_set_dense(lbm_ctx* c, const double* d_dense);
 cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense);
+cudaError_t launch_gfield_compact(lbm_ctx* c);
 cudaError_t launch_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, double* dL_dg, int dg_on_device,
                            double* dL_dtau, bool* started);
 }  // namespace lbm

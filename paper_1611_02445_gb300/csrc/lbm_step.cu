@@ -1,12 +1,15 @@
 // lbm_step.cu -- the fused collide-and-stream step kernel (Sec. 3.4, Algorithm 2).
 //
-// Work unit: a group of GROUP_TILES = 4 kept tiles, one thread per slot (256 threads;
-// thread s of a tile owns node x + 4 y + 16 z). Persistent CTAs walk the groups
-// b, b + G, b + 2G, ... with a software pipeline, so that while a group is computed the
-// next group's gathers are already in flight:
+// Work unit: a group of up to 8 consecutive kept tiles holding up to 256 non-solid
+// nodes, one thread per non-solid node (solid slots of a tile get no thread, so no warp
+// lane idles on them). Persistent CTAs walk the groups b, b + G, b + 2G, ... with a
+// software pipeline, so that while a group is computed the next group's gathers are
+// already in flight:
+//   header(g) cp.async of the group's {first tile, tiles, first node, nodes}, three
+//             groups ahead, into a 4-slot ring;
 //   meta(g)   cp.async of the group's neighbour records (the local tileMap copy of
-//             Algorithm 2, 28 ranks per tile) and per-node gather words (which
-//             directions bounce, node type) into a 3-slot shared-memory ring;
+//             Algorithm 2, 28 ranks per tile) and per-node words (which directions
+//             bounce, node type, tile and slot) into a 3-slot shared-memory ring;
 //   gather(g) every non-solid node pulls f_i from x - c_i -- its own tile's or a
 //             neighbour tile's data block i -- or, when the word says the source is
 //             solid, dropped or outside the box, its own A_inv(i)(x) (halfway
@@ -23,8 +26,8 @@
 
 namespace lbm {
 
-constexpr int GROUP_TILES = 4;
-constexpr int STEP_THREADS = GROUP_TILES * SLOTS;   // 256
+constexpr int STEP_THREADS = GROUP_MAX_NODES;   // 256: one thread per non-solid node
+constexpr int HDR_SLOTS = 4;
 constexpr int META_SLOTS = 3;
 constexpr int DATA_SLOTS = 2;
 
@@ -58,12 +61,15 @@ __device__ __forceinline__ void eq_pair(R& a, R& b, R w, R cu, R D, R rho, R uu1
 // One node's collision, in place on v[19].
 template <typename R, bool SHIFT>
 __device__ __forceinline__ void collide(R v[Q], int type, const StepParams& p, R Fx, R Fy, R Fz) {
-    const R sum = ((v[0] + v[1]) + (v[2] + v[3])) + ((v[4] + v[5]) + (v[6] + v[7])) +
-                  ((v[8] + v[9]) + (v[10] + v[11])) + ((v[12] + v[13]) + (v[14] + v[15])) +
-                  ((v[16] + v[17]) + v[18]);
-    const R jx = ((v[1] + v[7]) + (v[10] + v[11]) + v[12]) - ((v[3] + v[8]) + (v[9] + v[13]) + v[14]);
-    const R jy = ((v[2] + v[7]) + (v[8] + v[15]) + v[16]) - ((v[4] + v[9]) + (v[10] + v[17]) + v[18]);
-    const R jz = ((v[5] + v[11]) + (v[13] + v[15]) + v[17]) - ((v[6] + v[12]) + (v[14] + v[16]) + v[18]);
+    // moments from pair sums s and differences d of opposite directions
+    const R s13 = v[1] + v[3], s24 = v[2] + v[4], s56 = v[5] + v[6], s79 = v[7] + v[9], s810 = v[8] + v[10];
+    const R s1114 = v[11] + v[14], s1213 = v[12] + v[13], s1518 = v[15] + v[18], s1617 = v[16] + v[17];
+    const R d13 = v[1] - v[3], d24 = v[2] - v[4], d56 = v[5] - v[6], d79 = v[7] - v[9], d810 = v[8] - v[10];
+    const R d1114 = v[11] - v[14], d1213 = v[12] - v[13], d1518 = v[15] - v[18], d1617 = v[16] - v[17];
+    const R sum = ((v[0] + s13) + (s24 + s56)) + ((s79 + s810) + (s1114 + s1213)) + (s1518 + s1617);
+    const R jx = ((d13 + d79) - d810) + (d1114 + d1213);
+    const R jy = ((d24 + d79) + d810) + (d1518 + d1617);
+    const R jz = ((d56 + d1114) - d1213) + (d1518 - d1617);
     R D, rho;
     if (SHIFT) {
         D = sum + R(WF_BIAS);
@@ -78,7 +84,7 @@ __device__ __forceinline__ void collide(R v[Q], int type, const StepParams& p, R
     const R uz = (jz + R(0.5) * Fz) * inv_rho;
     const R w0 = R(wgt(0)), w1 = R(wgt(1)), w2 = R(wgt(7));
     if (type == LBM_FLUID) {
-        const R omega = R(p.omega), om1 = R(1) - omega, beta = R(p.beta);
+        const R omega = par<R>(p.omega, p.omega_f), om1 = R(1) - omega, beta = par<R>(p.beta, p.beta_f);
         const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
         const R uF3 = R(3) * (ux * Fx + uy * Fy + uz * Fz);
         v[0] = om1 * v[0] + (omega * (w0 * D - (w0 * rho) * uu15) - (beta * w0) * uF3);
@@ -95,12 +101,14 @@ __device__ __forceinline__ void collide(R v[Q], int type, const StepParams& p, R
         // inlet: f^eq(rho, u_in); outlet: f^eq(rho_out, u)
         R ex, ey, ez, Dq, rq;
         if (type == LBM_INLET) {
-            ex = R(p.u_in[0]); ey = R(p.u_in[1]); ez = R(p.u_in[2]);
+            ex = par<R>(p.u_in[0], p.u_in_f[0]);
+            ey = par<R>(p.u_in[1], p.u_in_f[1]);
+            ez = par<R>(p.u_in[2], p.u_in_f[2]);
             Dq = D; rq = rho;
         } else {
             ex = ux; ey = uy; ez = uz;
-            rq = R(p.rho_out);
-            Dq = SHIFT ? R(p.rho_out - 1.0) : rq;
+            rq = par<R>(p.rho_out, p.rho_out_f);
+            Dq = SHIFT ? par<R>(p.rho_out - 1.0, p.rho_out_m1_f) : rq;
         }
         const R uu15 = R(1.5) * (ex * ex + ey * ey + ez * ez);
         v[0] = w0 * Dq - (w0 * rq) * uu15;
@@ -142,48 +150,51 @@ template <int DT>
 struct StepSmem {
     using E = typename Staged<DT>::E;
     using G = typename Store<DT>::R;
-    int32_t nbr[META_SLOTS][GROUP_TILES][NBR_STRIDE];
+    int4 hdr[HDR_SLOTS];                                   // {t0, tiles, f0, nodes}
+    int32_t nbr[META_SLOTS][GROUP_MAX_TILES][NBR_STRIDE];
     uint32_t word[META_SLOTS][STEP_THREADS];
     G gf[META_SLOTS][STEP_THREADS];
     E data[DATA_SLOTS][Q][STEP_THREADS];
 };
 
+__device__ __forceinline__ void issue_hdr(int4* hdr, int64_t grp, int64_t n_groups, const int4* __restrict__ groups) {
+    if (threadIdx.x == 0 && grp < n_groups) cp_async16(hdr, groups + grp);
+}
+
+// Neighbour records of the group's tiles, and the words (and forces) of its nodes.
 template <int DT>
-__device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int slot, int64_t grp, int64_t n_tiles,
-                                           const int32_t* __restrict__ nbr, const uint32_t* __restrict__ nword,
-                                           const void* gfield) {
+__device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const int4 h, const int32_t* __restrict__ nbr,
+                                           const uint32_t* __restrict__ fword, const void* gfield_c) {
     const int t = threadIdx.x;
-    const int64_t k0 = grp * GROUP_TILES;
-    // neighbour records: GROUP_TILES x 112 bytes = 28 chunks of 16 bytes
-    if (t < GROUP_TILES * (NBR_STRIDE / 4)) {
+    if (t < h.y * (NBR_STRIDE / 4)) {
         const int lt = t / (NBR_STRIDE / 4), c = t % (NBR_STRIDE / 4);
-        if (k0 + lt < n_tiles) cp_async16(&sm.nbr[slot][lt][4 * c], nbr + (k0 + lt) * NBR_STRIDE + 4 * c);
+        cp_async16(&sm.nbr[mslot][lt][4 * c], nbr + (int64_t)(h.x + lt) * NBR_STRIDE + 4 * c);
     }
-    const int64_t k = k0 + (t >> 6);
-    if (k < n_tiles) {
-        cp_async4(&sm.word[slot][t], nword + k * SLOTS + (t & 63));
-        if (gfield) {
-            const typename Store<DT>::R* g = static_cast<const typename Store<DT>::R*>(gfield);
-            if (DT == LBM_F64) cp_async8(&sm.gf[slot][t], g + k * SLOTS + (t & 63));
-            else cp_async4(&sm.gf[slot][t], g + k * SLOTS + (t & 63));
+    if (t < h.w) {
+        cp_async4(&sm.word[mslot][t], fword + h.z + t);
+        if (gfield_c) {
+            const typename Store<DT>::R* g = static_cast<const typename Store<DT>::R*>(gfield_c);
+            if (DT == LBM_F64) cp_async8(&sm.gf[mslot][t], g + h.z + t);
+            else cp_async4(&sm.gf[mslot][t], g + h.z + t);
         }
     } else {
-        sm.word[slot][t] = 0;   // past the last tile: treated as solid
+        sm.word[mslot][t] = 0;   // no node: idle thread
     }
 }
 
-// Issue the 19 gathers of this thread's node of group grp. Returns, for F16S, the mask
-// of directions whose half is the upper half of the staged word.
+// Issue the 19 gathers of this thread's node. Returns, for F16S, the mask of directions
+// whose half is the upper half of the staged word.
 template <int DT>
-__device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, int dslot, int64_t grp,
+__device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, int dslot, const int4 h,
                                                  const typename Store<DT>::T* __restrict__ A) {
     using T = typename Store<DT>::T;
-    const int t = threadIdx.x, lt = t >> 6, s = t & 63;
+    const int t = threadIdx.x;
     const uint32_t w = sm.word[mslot][t];
     uint32_t odd = 0;
-    if ((w >> WORD_TYPE_SHIFT) == LBM_SOLID) return 0;
+    if (((w >> WORD_TYPE_SHIFT) & 3u) == LBM_SOLID) return 0;
+    const int lt = (int)((w >> WORD_LT_SHIFT) & 7u), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
-    const int64_t own = (grp * GROUP_TILES + lt) * (Q * SLOTS);
+    const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         int64_t src;
@@ -207,15 +218,17 @@ __device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, in
     return odd;
 }
 
-template <int DT>
-__device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, int64_t grp, uint32_t odd,
-                                              typename Store<DT>::T* __restrict__ B, const StepParams& p) {
+template <int DT, bool NATIVE>
+__device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, uint32_t odd,
+                                              typename Store<DT>::T* __restrict__ B, const StepParams& p,
+                                              bool has_gf) {
     using R = typename Store<DT>::R;
     using T = typename Store<DT>::T;
-    const int t = threadIdx.x, lt = t >> 6, s = t & 63;
+    const int t = threadIdx.x;
     const uint32_t w = sm.word[mslot][t];
-    const int type = (int)(w >> WORD_TYPE_SHIFT);
+    const int type = (int)((w >> WORD_TYPE_SHIFT) & 3u);
     if (type == LBM_SOLID) return;
+    const int lt = (int)((w >> WORD_LT_SHIFT) & 7u), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     R v[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -230,87 +243,104 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
         }
         v[i] = to_arith<DT>(e, i);
     }
-    const R Fx = p.gfield ? sm.gf[mslot][t] : R(p.g[0]);
-    collide<R, Store<DT>::SHIFT>(v, type, p, Fx, R(p.g[1]), R(p.g[2]));
-    const int64_t own = (grp * GROUP_TILES + lt) * (Q * SLOTS);
+    const R Fx = has_gf ? sm.gf[mslot][t] : par<R>(p.g[0], p.g_f[0]);
+    const R Fy = par<R>(p.g[1], p.g_f[1]), Fz = par<R>(p.g[2], p.g_f[2]);
+    if constexpr (DT == LBM_F64 && !NATIVE) {
+        // FP64 storage: double-float collision for fluid nodes, FP64 for the closures
+        if (type == LBM_FLUID) collide_df(v, (double)Fx, p.dfc);
+        else collide<R, false>(v, type, p, Fx, Fy, Fz);
+    } else {
+        collide<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
+    }
+    const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
 #pragma unroll
     for (int i = 0; i < Q; i++) B[own + i * SLOTS + s] = to_store<DT>(v[i], i);
 }
 
 // Resident CTAs per SM the kernel is compiled for: shared memory allows 4 CTAs of the
-// 4-byte formats (46 KB each) and 2 of FP64 (88 KB each); registers are capped to match.
+// 4-byte formats (about 46 KB each) and 2 of FP64 (about 88 KB each); registers match.
 template <int DT> struct StepOcc { static constexpr int CTAS = 4; };
 template <> struct StepOcc<LBM_F64> { static constexpr int CTAS = 2; };
 
-template <int DT>
+template <int DT, bool NATIVE>
 __global__ void __launch_bounds__(STEP_THREADS, StepOcc<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
-       const int32_t* __restrict__ nbr, const uint32_t* __restrict__ nword, int64_t n_tiles,
-       int64_t n_groups, StepParams p) {
+       const int4* __restrict__ groups, const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
+       const void* __restrict__ gfield_c, int64_t n_groups, StepParams p) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<DT>& sm = *reinterpret_cast<StepSmem<DT>*>(smem_raw);
     const int64_t G = gridDim.x;
     const int64_t g0 = blockIdx.x;
     if (g0 >= n_groups) return;
-    // prologue: meta(g0), meta(g0 + G), then gather(g0)
-    issue_meta<DT>(sm, 0, g0, n_tiles, nbr, nword, p.gfield);
+    const bool has_gf = gfield_c != nullptr;
+    // prologue: headers of groups 0..2, meta of groups 0..1, gathers of group 0
+    issue_hdr(&sm.hdr[0], g0, n_groups, groups);
     cp_async_commit();
-    if (g0 + G < n_groups) issue_meta<DT>(sm, 1, g0 + G, n_tiles, nbr, nword, p.gfield);
+    issue_hdr(&sm.hdr[1], g0 + G, n_groups, groups);
+    cp_async_commit();
+    issue_hdr(&sm.hdr[2], g0 + 2 * G, n_groups, groups);
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+    issue_meta<DT>(sm, 0, sm.hdr[0], nbr, fword, gfield_c);
+    cp_async_commit();
+    if (g0 + G < n_groups) issue_meta<DT>(sm, 1, sm.hdr[1], nbr, fword, gfield_c);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    uint32_t odd_cur = issue_gather<DT>(sm, 0, 0, g0, A);
+    uint32_t odd_cur = issue_gather<DT>(sm, 0, 0, sm.hdr[0], A);
     cp_async_commit();
     int it = 0;
     for (int64_t g = g0; g < n_groups; g += G, it++) {
-        const int m_cur = it % META_SLOTS, m_next = (it + 1) % META_SLOTS, m_next2 = (it + 2) % META_SLOTS;
-        const int d_cur = it & 1, d_next = (it + 1) & 1;
-        // pending: meta(g + G), gather(g)
+        // pending: header(g + 2G) [done], meta(g + G), gather(g)
         cp_async_wait<1>();
-        __syncthreads();   // meta(g + G) visible; everyone done with iteration it - 1
-        if (g + 2 * G < n_groups) issue_meta<DT>(sm, m_next2, g + 2 * G, n_tiles, nbr, nword, p.gfield);
+        __syncthreads();   // header(g + 2G), meta(g + G) visible; iteration it - 1 finished
+        issue_hdr(&sm.hdr[(it + 3) & 3], g + 3 * G, n_groups, groups);
+        cp_async_commit();
+        if (g + 2 * G < n_groups) issue_meta<DT>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], nbr, fword, gfield_c);
         cp_async_commit();
         uint32_t odd_next = 0;
-        if (g + G < n_groups) odd_next = issue_gather<DT>(sm, m_next, d_next, g + G, A);
+        if (g + G < n_groups)
+            odd_next = issue_gather<DT>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
         cp_async_commit();
-        // pending: gather(g), meta(g + 2G), gather(g + G)
-        cp_async_wait<2>();
-        compute_store<DT>(sm, m_cur, d_cur, g, odd_cur, B, p);
+        // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
+        cp_async_wait<3>();
+        compute_store<DT, NATIVE>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], odd_cur, B, p, has_gf);
         odd_cur = odd_next;
     }
     cp_async_wait<0>();
 }
 
-template <int DT>
+template <int DT, bool NATIVE>
 static int step_grid(int64_t n_groups) {
     static int per_sm = -1, n_sm = 0;
     if (per_sm < 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_step<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StepSmem<DT>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT>, STEP_THREADS, sizeof(StepSmem<DT>));
+        cudaFuncSetAttribute(k_step<DT, NATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StepSmem<DT>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, NATIVE>, STEP_THREADS, sizeof(StepSmem<DT>));
         if (per_sm < 1) per_sm = 1;
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)per_sm * n_sm));
 }
 
-template <int DT>
+template <int DT, bool NATIVE>
 static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
-    const int64_t n_groups = (c->n_tiles + GROUP_TILES - 1) / GROUP_TILES;
-    const int grid = step_grid<DT>(n_groups);
-    k_step<DT><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
-        (const T*)A, (T*)B, c->nbr, c->nword, c->n_tiles, n_groups, c->p);
+    const int grid = step_grid<DT, NATIVE>(c->n_groups);
+    k_step<DT, NATIVE><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
+        (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B) {
-    if (c->n_tiles == 0) return cudaSuccess;
+    if (c->n_groups == 0) return cudaSuccess;
     switch (c->dtype) {
-        case LBM_F64: return launch_step_dt<LBM_F64>(c, A, B);
-        case LBM_F32: return launch_step_dt<LBM_F32>(c, A, B);
-        default: return launch_step_dt<LBM_F16S>(c, A, B);
+        case LBM_F64:
+            return c->native64 ? launch_step_dt<LBM_F64, true>(c, A, B) : launch_step_dt<LBM_F64, false>(c, A, B);
+        case LBM_F32: return launch_step_dt<LBM_F32, false>(c, A, B);
+        default: return launch_step_dt<LBM_F16S, false>(c, A, B);
     }
 }
 

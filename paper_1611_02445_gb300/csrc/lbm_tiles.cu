@@ -529,6 +529,25 @@ __global__ void k_gfield(G* __restrict__ gt, const double* __restrict__ dense, c
     }
 }
 
+// Tile-major force -> the compact per-fluid-node copy read by the step kernel.
+template <typename G>
+__global__ void k_gfield_compact(G* __restrict__ gc, const G* __restrict__ gt, const uint32_t* __restrict__ fidx,
+                                 int64_t n_fluid) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < n_fluid; n += (int64_t)gridDim.x * blockDim.x)
+        gc[n] = gt[fidx[n]];
+}
+
+cudaError_t launch_gfield_compact(lbm_ctx* c) {
+    const unsigned g = grid_for(c->n_nonsolid, 256);
+    if (c->dtype == LBM_F64)
+        k_gfield_compact<double><<<g, 256, 0, c->stream>>>((double*)c->gfield_c, (const double*)c->gfield, c->fidx,
+                                                           c->n_nonsolid);
+    else
+        k_gfield_compact<float><<<g, 256, 0, c->stream>>>((float*)c->gfield_c, (const float*)c->gfield, c->fidx,
+                                                          c->n_nonsolid);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense) {
     const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
     if (c->dtype == LBM_F64)

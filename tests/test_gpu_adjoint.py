@@ -1,11 +1,14 @@
 """GPU adjoint (lbm_adjoint, through the C ABI) against the oracle adjoint and against
 central finite differences of the GPU's own FP64 forward.
 
-Bars: FP64 storage -- loss to 1e-12 relative, gradients to 1e-10 of their largest
-entry (the kernels reorder sums and contract multiply-adds); checkpoint spacing
-changes nothing (the recompute is deterministic); finite differences with a relative
-step of 1e-3 agree to 1e-4 relative. FP32 storage -- the error against the FP64
-oracle adjoint is stated and bounded.
+Bars: FP64 storage with FP64 arithmetic ("f64n") -- loss to 1e-12 relative, gradients
+to 1e-10 of their largest entry (the kernels reorder sums and contract multiply-adds).
+FP64 storage with the double-float collision ("f64") -- per-distribution parity of
+1e-12 w_i bounds the velocity error by 1e-12 * sum_i |c_ix| w_i = 3.3e-13 absolute, which
+is the loss bar; gradients to 1e-9 of their largest entry. Checkpoint spacing changes
+nothing (the recompute is deterministic); finite differences with a relative step of
+1e-3 agree to 1e-4 relative. FP32 storage -- the error against the FP64 oracle adjoint
+is stated and bounded.
 """
 import numpy as np
 import pytest
@@ -18,6 +21,18 @@ from paper_1611_02445_gb300 import lbm
 pytestmark = pytest.mark.gpu
 
 KW = dict(u_in=(0.04, 0.01, 0.0), rho_out=1.01)
+LOSS_ABS_DF = 1e-12 / 3.0
+
+
+def check_loss(Lg, Lo, dtype):
+    if dtype == "f64n":
+        assert abs(Lg - Lo) <= 1e-12 * max(abs(Lo), 1e-30)
+    else:
+        assert abs(Lg - Lo) <= LOSS_ABS_DF
+
+
+def grad_tol(dtype):
+    return 1e-10 if dtype == "f64n" else 1e-9
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -39,21 +54,22 @@ def gpu_adjoint(nt, f0, T, K, plane, periodic, tau, g=(0, 0, 0), gf=None, u_in=(
         return L.adjoint(T, K, plane, grads)
 
 
+@pytest.mark.parametrize("dtype", ["f64n", "f64"])
 @pytest.mark.parametrize("periodic,boundary", [(0b111, False), (0b000, True), (0b011, True)])
-def test_adjoint_f64_matches_oracle(periodic, boundary):
+def test_adjoint_f64_matches_oracle(periodic, boundary, dtype):
     nt = I.random_box(8, 8, 12, p_solid=0.25, seed=periodic + 3, boundary=boundary)
     rng = np.random.default_rng(periodic)
     gf = 1e-3 * (1 + 0.1 * rng.standard_normal(nt.shape))
     f0 = I.random_populations(nt, 0.05, seed=periodic + 9)
     T, K, plane, tau = 7, 3, 7, 0.8
     g = (0.0, 1e-4, -2e-4)
-    Lg, dg, dtau = gpu_adjoint(nt, f0, T, K, plane, periodic, tau, g, gf, **KW)
+    Lg, dg, dtau = gpu_adjoint(nt, f0, T, K, plane, periodic, tau, g, gf, dtype=dtype, **KW)
     Lo, dg_o, _, dtau_o = O.adjoint(nt, T, plane, periodic, tau, g, gf, f0=f0, **KW)
-    assert abs(Lg - Lo) <= 1e-12 * max(abs(Lo), 1e-30)
+    check_loss(Lg, Lo, dtype)
     m = nt != 0
-    assert np.abs(dg[m] - dg_o[m]).max() <= 1e-10 * np.abs(dg_o).max()
+    assert np.abs(dg[m] - dg_o[m]).max() <= grad_tol(dtype) * np.abs(dg_o).max()
     assert (dg[~m] == 0).all()
-    assert abs(dtau - dtau_o) <= 1e-10 * abs(dtau_o)
+    assert abs(dtau - dtau_o) <= grad_tol(dtype) * abs(dtau_o)
 
 
 def test_adjoint_checkpoint_spacing_changes_nothing():
@@ -70,21 +86,22 @@ def test_adjoint_checkpoint_spacing_changes_nothing():
             assert np.array_equal(out[1], ref[1])
 
 
-def test_adjoint_loss_only_and_state_after():
+@pytest.mark.parametrize("dtype", ["f64n", "f64"])
+def test_adjoint_loss_only_and_state_after(dtype):
     nt = I.random_box(8, 8, 8, p_solid=0.2, seed=5)
-    with lbm.Lattice(nt, "f64", 0b111) as L:
+    with lbm.Lattice(nt, dtype, 0b111) as L:
         L.set_params(0.8, (1e-4, 0, 0))
         L.init_equilibrium()
         Lonly, dg, dtau = L.adjoint(5, 2, 3, grads=False)
         f_after = L.get_f()
         assert dg is None and dtau is None
-    with lbm.Lattice(nt, "f64", 0b111) as L:
+    with lbm.Lattice(nt, dtype, 0b111) as L:
         L.set_params(0.8, (1e-4, 0, 0))
         L.init_equilibrium()
         L.step(5)
         assert np.array_equal(L.get_f(), f_after, equal_nan=True)
     fo = O.run(O.init(nt), nt, 5, 0b111, 0.8, (1e-4, 0, 0))
-    assert abs(Lonly - O.loss(fo, nt, 3, (1e-4, 0, 0))[0]) <= 1e-12 * abs(Lonly)
+    check_loss(Lonly, O.loss(fo, nt, 3, (1e-4, 0, 0))[0], dtype)
 
 
 def _crop_case():
@@ -98,12 +115,13 @@ def test_adjoint_crop32_f64_and_f32_vs_oracle():
     nt, gf = _crop_case()
     T, K, plane, tau = 40, 16, 31, 0.8
     Lo, dg_o, _, dtau_o = O.adjoint(nt, T, plane, 0b111, tau, g_field=gf)
-    Lg, dg, dtau = gpu_adjoint(nt, None, T, K, plane, 0b111, tau, gf=gf)
     m = nt != 0
     scale = np.abs(dg_o).max()
-    assert abs(Lg - Lo) <= 1e-12 * abs(Lo)
-    assert np.abs(dg[m] - dg_o[m]).max() <= 1e-10 * scale
-    assert abs(dtau - dtau_o) <= 1e-10 * abs(dtau_o)
+    for dtype in ("f64n", "f64"):
+        Lg, dg, dtau = gpu_adjoint(nt, None, T, K, plane, 0b111, tau, gf=gf, dtype=dtype)
+        check_loss(Lg, Lo, dtype)
+        assert np.abs(dg[m] - dg_o[m]).max() <= grad_tol(dtype) * scale
+        assert abs(dtau - dtau_o) <= grad_tol(dtype) * abs(dtau_o)
     L32, dg32, dtau32 = gpu_adjoint(nt, None, T, K, plane, 0b111, tau, gf=gf, dtype="f32")
     e_L = abs(L32 - Lo) / abs(Lo)
     e_g = np.abs(dg32[m] - dg_o[m]).max() / scale
