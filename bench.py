@@ -217,6 +217,9 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f64n", "f32", "f16s"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--kernel", default="full", choices=["full", "propagate", "rw"],
+                    help="the fused step, or one of the paper's calibration kernels (propagation "
+                         "only, read/write only)")
     ap.add_argument("--adjoint", action="store_true", help="run the adjoint workload instead")
     ap.add_argument("--adj-steps", type=int, default=2000)
     ap.add_argument("--size", type=int, default=256,
@@ -260,7 +263,8 @@ def main():
     L.set_params(tau, g)
     L.init_equilibrium()
     n_nonsolid = info["n_nonsolid"]
-    L.step(args.warmup)
+    kind = {"full": lbm.KERNEL_FULL, "propagate": lbm.KERNEL_PROPAGATE, "rw": lbm.KERNEL_RW}[args.kernel]
+    L.step_kernel(kind, args.warmup)
     torch.cuda.synchronize()
 
     def barrier():
@@ -275,7 +279,7 @@ def main():
     sampler.start()
     time.sleep(0.3)
     ev0.record(stream)
-    L.step(args.steps)
+    L.step_kernel(kind, args.steps)
     ev1.record(stream)
     torch.cuda.synchronize()
     clocks = sampler.stop()
@@ -287,6 +291,8 @@ def main():
     ms_max = float(t.item())
     mass, _ = L.reduce()
     assert np.isfinite(mass)
+    if args.kernel != "full":
+        args.no_e2e = True
     value = n_nonsolid * args.steps * world / (ms_max * 1e-3) / 1e6
 
     # roofline of the step kernel: algorithmic bytes B_node = 2 * 19 * n_d per non-solid
@@ -302,9 +308,9 @@ def main():
             "peak_source": f"{peak_src} hbm_gbs (STREAM-style copy)",
             "algorithmic_bytes_per_launch": alg_bytes}
     if args.dtype == "f64n":
-        # FP64 arithmetic bounds this kernel on GB300: FP64 FLOPs executed per non-solid
-        # node update, counted with ncu (2 * dfma + dadd + dmul per node), over the FP64
-        # peak of 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz.
+        # FP64 arithmetic throughout bounds this kernel on GB300: FP64 FLOPs executed per
+        # non-solid node update, counted with ncu (2 * dfma + dadd + dmul per node), over the
+        # FP64 peak of 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz.
         flops_per_node = FP64_FLOPS_PER_NODE
         fp64_peak = 152 * 2 * 2 * 2.07e9 / 1e12
         achieved_tf = n_nonsolid * flops_per_node / launch_s / 1e12
@@ -313,11 +319,21 @@ def main():
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (probe measured 1.20)",
                 "fp64_flops_per_node_update": flops_per_node,
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak}}
+    roof["traffic"] = TRAFFIC_PER_NODE.get(args.dtype) if args.kernel == "full" else None
+    if roof["traffic"] is not None and args.size == 256:
+        roof["traffic"] = roof["traffic"] * n_nonsolid
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 128^3 "
+                                  "pack, per non-solid node, times this launch's non-solid nodes")
+    else:
+        roof["traffic"] = None
 
     line = {"metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD if args.size == 256 else WORKLOAD.replace("256^3", f"{args.size}^3"),
+                       "kernel": {"full": "fused collide-and-stream step",
+                                  "propagate": "calibration: propagation only (gather with bounce-back, store)",
+                                  "rw": "calibration: read/write only (own values, no propagation)"}[args.kernel],
                        "storage": DTYPE_NAME[args.dtype], "n_nonsolid": n_nonsolid,
                        "n_tiles": info["n_tiles"], "eta_t": info["eta_t"],
                        "state_bytes": 2 * info["copy_bytes"],
@@ -364,9 +380,14 @@ def main():
         dist.destroy_process_group()
 
 
-# Executed FP64 FLOPs per non-solid node update of the FP64 step kernel: ncu counts of
-# 2 * dfma + dadd + dmul over one launch on the 128^3 pack, divided by its 732 512 nodes.
+# Executed FP64 FLOPs per non-solid node update of the all-FP64 step kernel: ncu counts
+# of 2 * dfma + dadd + dmul over one launch on the 128^3 pack, divided by its 732 512 nodes.
 FP64_FLOPS_PER_NODE = 331
+
+# DRAM bytes (read + write) per non-solid node of one step launch, from ncu on the 128^3
+# pack (scaled to a launch by the number of non-solid nodes); None where not captured for
+# the current kernel.
+TRAFFIC_PER_NODE = {"f64": (232.067072e6 + 107.181312e6) / 732512}
 
 if __name__ == "__main__":
     main()

@@ -114,6 +114,15 @@ lbm_status lbm_init_equilibrium(lbm_ctx* ctx, double rho0, const double* u0);
  * current copy and writing the other, then swapping them (Sec. 3.1). */
 lbm_status lbm_step(lbm_ctx* ctx, int n);
 
+/* The paper's calibration kernels (Sec. 4.1), which bound what the fused step can reach
+ * with this data layout: LBM_KERNEL_PROPAGATE gathers with bounce-back exactly as the
+ * step does and stores the gathered values without collision ("propagation only");
+ * LBM_KERNEL_RW reads and writes each node's own 19 values ("read/write only", no
+ * propagation). LBM_KERNEL_FULL is lbm_step. Same launch shape and A/B swap as lbm_step.
+ * The populations afterwards are not a physical state for the calibration kinds. */
+enum { LBM_KERNEL_FULL = 0, LBM_KERNEL_PROPAGATE = 1, LBM_KERNEL_RW = 2 };
+lbm_status lbm_step_kernel(lbm_ctx* ctx, int kind, int n);
+
 /* Density and velocity from the stored post-collision populations f*:
  * rho = sum_i f*_i, u = (sum_i c_i f*_i - F/2) / rho (Eq. 5 with the half-force shift of
  * Guo forcing); 0 at solid nodes. rho: nx*ny*nz values, u: 3*nx*ny*nz values, dense,

@@ -399,6 +399,18 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
     return LBM_OK;
 }
 
+lbm_status lbm_step_kernel(lbm_ctx* c, int kind, int n) {
+    LBM_CHECK_CTX(c);
+    if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
+    if (kind < LBM_KERNEL_FULL || kind > LBM_KERNEL_RW) return fail(c, LBM_EINVAL, "unknown kernel kind");
+    if (!c->state_set || !c->params_set) return fail(c, LBM_ESTATE, "set parameters and a state before stepping");
+    for (int k = 0; k < n; k++) {
+        LBM_CUDA(c, lbm::launch_step_kind(c, kind, c->f[c->cur], c->f[1 - c->cur]));
+        c->cur ^= 1;
+    }
+    return LBM_OK;
+}
+
 lbm_status lbm_reduce(lbm_ctx* c, double* mass, double* momentum) {
     LBM_CHECK_CTX(c);
     if (!c->state_set) return fail(c, LBM_ESTATE, "no state");

@@ -45,6 +45,10 @@ constexpr int WORD_TYPE_SHIFT = 20;
 constexpr int WORD_LT_SHIFT = 22;      // compact words: tile within the group (3 bits)
 constexpr int WORD_SLOT_SHIFT = 25;    // compact words: slot in the tile (6 bits)
 constexpr int GROUP_MAX_TILES = 8;
+// kernel kinds: the fused step and the paper's two calibration kernels (Sec. 4.1)
+constexpr int STEP_FULL = 0;        // gather, collide, store
+constexpr int STEP_PROPAGATE = 1;   // gather with bounce-back and store ("propagation only")
+constexpr int STEP_RW = 2;          // read and write each node's own values ("read/write only")
 constexpr int GROUP_MAX_NODES = 256;
 constexpr int FLAG_HAS_BC = 1;
 // F16S storage scale: h is stored as half(h * 2^12), so |h| in [1.5e-8, 16] is normal.
@@ -162,6 +166,7 @@ cudaError_t launch_tile_meta(lbm_ctx* c, const uint8_t* nt);
 cudaError_t launch_node_words(lbm_ctx* c);
 cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]);
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B);
+cudaError_t launch_step_kind(lbm_ctx* c, int kind, const void* A, void* B);
 cudaError_t launch_reduce(lbm_ctx* c, double* d_out);
 cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64);
 cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* d_out);

@@ -184,7 +184,7 @@ __device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const in
 
 // Issue the 19 gathers of this thread's node. Returns, for F16S, the mask of directions
 // whose half is the upper half of the staged word.
-template <int DT>
+template <int DT, int MODE>
 __device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, int dslot, const int4 h,
                                                  const typename Store<DT>::T* __restrict__ A) {
     using T = typename Store<DT>::T;
@@ -198,7 +198,9 @@ __device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, in
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         int64_t src;
-        if ((w >> i) & 1) {
+        if (MODE == STEP_RW) {
+            src = own + i * SLOTS + s;   // read/write only: the node's own values
+        } else if ((w >> i) & 1) {
             src = own + inv(i) * SLOTS + s;
         } else {
             const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
@@ -218,7 +220,7 @@ __device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, in
     return odd;
 }
 
-template <int DT, bool NATIVE>
+template <int DT, bool NATIVE, int MODE>
 __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, uint32_t odd,
                                               typename Store<DT>::T* __restrict__ B, const StepParams& p,
                                               bool has_gf) {
@@ -245,7 +247,9 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     }
     const R Fx = has_gf ? sm.gf[mslot][t] : par<R>(p.g[0], p.g_f[0]);
     const R Fy = par<R>(p.g[1], p.g_f[1]), Fz = par<R>(p.g[2], p.g_f[2]);
-    if constexpr (DT == LBM_F64 && !NATIVE) {
+    if constexpr (MODE != STEP_FULL) {
+        // calibration kernels: no collision, the gathered values are stored as they are
+    } else if constexpr (DT == LBM_F64 && !NATIVE) {
         // FP64 storage: double-float collision for fluid nodes, FP64 for the closures
         if (type == LBM_FLUID) collide_df(v, (double)Fx, p.dfc);
         else collide<R, false>(v, type, p, Fx, Fy, Fz);
@@ -262,7 +266,7 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
 template <int DT> struct StepOcc { static constexpr int CTAS = 4; };
 template <> struct StepOcc<LBM_F64> { static constexpr int CTAS = 2; };
 
-template <int DT, bool NATIVE>
+template <int DT, bool NATIVE, int MODE>
 __global__ void __launch_bounds__(STEP_THREADS, StepOcc<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
@@ -288,7 +292,7 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    uint32_t odd_cur = issue_gather<DT>(sm, 0, 0, sm.hdr[0], A);
+    uint32_t odd_cur = issue_gather<DT, MODE>(sm, 0, 0, sm.hdr[0], A);
     cp_async_commit();
     int it = 0;
     for (int64_t g = g0; g < n_groups; g += G, it++) {
@@ -301,46 +305,60 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         cp_async_commit();
         uint32_t odd_next = 0;
         if (g + G < n_groups)
-            odd_next = issue_gather<DT>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
+            odd_next = issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
         cp_async_commit();
         // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
         cp_async_wait<3>();
-        compute_store<DT, NATIVE>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], odd_cur, B, p, has_gf);
+        compute_store<DT, NATIVE, MODE>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], odd_cur, B, p, has_gf);
         odd_cur = odd_next;
     }
     cp_async_wait<0>();
 }
 
-template <int DT, bool NATIVE>
+template <int DT, bool NATIVE, int MODE>
 static int step_grid(int64_t n_groups) {
     static int per_sm = -1, n_sm = 0;
     if (per_sm < 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_step<DT, NATIVE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StepSmem<DT>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, NATIVE>, STEP_THREADS, sizeof(StepSmem<DT>));
+        cudaFuncSetAttribute(k_step<DT, NATIVE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(StepSmem<DT>));
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, NATIVE, MODE>, STEP_THREADS,
+                                                      sizeof(StepSmem<DT>));
         if (per_sm < 1) per_sm = 1;
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)per_sm * n_sm));
 }
 
-template <int DT, bool NATIVE>
+template <int DT, bool NATIVE, int MODE>
 static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
-    const int grid = step_grid<DT, NATIVE>(c->n_groups);
-    k_step<DT, NATIVE><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
+    const int grid = step_grid<DT, NATIVE, MODE>(c->n_groups);
+    k_step<DT, NATIVE, MODE><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
         (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p);
     return cudaGetLastError();
 }
 
-cudaError_t launch_step(lbm_ctx* c, const void* A, void* B) {
-    if (c->n_groups == 0) return cudaSuccess;
+template <int MODE>
+static cudaError_t launch_step_mode(lbm_ctx* c, const void* A, void* B) {
     switch (c->dtype) {
         case LBM_F64:
-            return c->native64 ? launch_step_dt<LBM_F64, true>(c, A, B) : launch_step_dt<LBM_F64, false>(c, A, B);
-        case LBM_F32: return launch_step_dt<LBM_F32, false>(c, A, B);
-        default: return launch_step_dt<LBM_F16S, false>(c, A, B);
+            return c->native64 ? launch_step_dt<LBM_F64, true, MODE>(c, A, B)
+                               : launch_step_dt<LBM_F64, false, MODE>(c, A, B);
+        case LBM_F32: return launch_step_dt<LBM_F32, false, MODE>(c, A, B);
+        default: return launch_step_dt<LBM_F16S, false, MODE>(c, A, B);
+    }
+}
+
+cudaError_t launch_step(lbm_ctx* c, const void* A, void* B) { return launch_step_kind(c, STEP_FULL, A, B); }
+
+cudaError_t launch_step_kind(lbm_ctx* c, int kind, const void* A, void* B) {
+    if (c->n_groups == 0) return cudaSuccess;
+    switch (kind) {
+        case STEP_PROPAGATE: return launch_step_mode<STEP_PROPAGATE>(c, A, B);
+        case STEP_RW: return launch_step_mode<STEP_RW>(c, A, B);
+        default: return launch_step_mode<STEP_FULL>(c, A, B);
     }
 }
 

@@ -59,6 +59,7 @@ def load():
     L.lbm_set_params.argtypes = [vp, d, pd, vp, i, pd, d]
     L.lbm_init_equilibrium.argtypes = [vp, d, pd]
     L.lbm_step.argtypes = [vp, i]
+    L.lbm_step_kernel.argtypes = [vp, i, i]
     L.lbm_macroscopic.argtypes = [vp, vp, vp, i, i]
     L.lbm_reduce.argtypes = [vp, pd, pd]
     L.lbm_get_f_box.argtypes = [vp, i, i, i, i, i, i, vp]
@@ -163,6 +164,13 @@ def lbm_init_equilibrium(ctx, rho0=1.0, u0=None):
 
 def lbm_step(ctx, n=1):
     _check(load().lbm_step(ctx, int(n)), ctx)
+
+
+KERNEL_FULL, KERNEL_PROPAGATE, KERNEL_RW = 0, 1, 2
+
+
+def lbm_step_kernel(ctx, kind, n=1):
+    _check(load().lbm_step_kernel(ctx, int(kind), int(n)), ctx)
 
 
 def lbm_macroscopic(ctx, rho, u, out_f64=True):
@@ -294,6 +302,9 @@ class Lattice:
 
     def step(self, n=1):
         lbm_step(self.ctx, n)
+
+    def step_kernel(self, kind, n=1):
+        lbm_step_kernel(self.ctx, kind, n)
 
     def set_stream(self, stream):
         lbm_set_stream(self.ctx, stream)

@@ -292,3 +292,37 @@ def test_vessel_crop_inlet_outlet_parity(dtype):
     f0 = O.init(nt)
     fg, fo, _, _ = run_pair(nt, f0, 100, 0, 0.6, (0, 0, 0), None, (0.05, 0, 0), 1.0, dtype=dtype)
     assert rel_err(fg, fo, nt) <= F64_TOL
+
+
+# ------------------------------------------------- calibration kernels (Sec. 4.1)
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_propagation_only_kernel_is_pure_streaming(dtype):
+    """With the collision left out the step is the streaming permutation with halfway
+    bounce-back: the oracle's step with tau = inf and F = 0, bit for bit (on values already
+    representable in the storage format). Fluid and solid nodes only: the oracle applies
+    the inlet/outlet closures whatever tau is."""
+    import math
+    nt = I.random_box(12, 8, 16, p_solid=0.35, seed=31, boundary=False)
+    f0 = I.random_populations(nt, 0.05, seed=32)
+    with lbm.Lattice(nt, dtype, 0b101) as L:
+        L.set_params(0.8)
+        L.set_f(f0)
+        f_in = L.get_f()                     # f0 rounded to the storage format
+        L.step_kernel(lbm.KERNEL_PROPAGATE, 3)
+        fg = L.get_f()
+    fo = O.run(f_in, nt, 3, 0b101, math.inf)
+    m = nt != 0
+    assert np.array_equal(fg[:, m], fo[:, m])
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32", "f16s"])
+def test_read_write_only_kernel_is_identity(dtype):
+    nt = I.random_box(12, 8, 16, p_solid=0.35, seed=33)
+    f0 = I.random_populations(nt, 0.05, seed=34)
+    with lbm.Lattice(nt, dtype, 0b111) as L:
+        L.set_params(0.8)
+        L.set_f(f0)
+        f_in = L.get_f()
+        L.step_kernel(lbm.KERNEL_RW, 5)
+        fg = L.get_f()
+    assert np.array_equal(fg, f_in, equal_nan=True)
