@@ -208,6 +208,140 @@ def run_adjoint_workload(args):
     print(json.dumps(line), flush=True)
 
 
+def _timed_steps(L, n, stream):
+    import torch
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    L.step(n)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    return ev0.elapsed_time(ev1)
+
+
+def run_poiseuille(args):
+    """Plane Poiseuille 32^3 (walls y = 0, 31; periodic x, z; tau 0.8; g_x 1e-6), FP64:
+    MFLUPS over 1000 steps (CUDA-graph replay; the problem is launch-bound), then the error
+    of u_x against g/(2 nu) (y - 1/2)(30.5 - y) at 1000 steps (start-up, not steady) and
+    at 12 000 steps, and the relative mass drift."""
+    import torch
+    import __graft_entry__
+    from paper_1611_02445_gb300 import inputs as I
+    from paper_1611_02445_gb300 import lbm
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    nt = I.poiseuille_channel(32, 32, 32)
+    tau, g = 0.8, 1e-6
+    nu = (tau - 0.5) / 3.0
+    y = np.arange(1, 31, dtype=np.float64)
+    exact = g / (2 * nu) * (y - 0.5) * (30.5 - y)
+    out = {"workload": "plane Poiseuille 32^3, walls y=0,31, periodic x,z, tau 0.8, g_x 1e-6, FP64 storage"}
+    for dtype in ("f64", "f64n"):
+        with lbm.Lattice(nt, dtype, 0b101, stream) as L:
+            L.set_params(tau, (g, 0.0, 0.0))
+            L.init_equilibrium()
+            m0, _ = L.reduce()
+            L.step(args.warmup)
+            ms = _timed_steps(L, 1000, stream)
+            n = L.info()["n_nonsolid"]
+            res = {"mflups": n * 1000 / (ms * 1e-3) / 1e6, "ms_per_step": ms / 1000}
+            L.init_equilibrium()
+            for total in (1000, 12000):
+                L.step(total - (0 if total == 1000 else 1000))
+                rho, u = L.macroscopic()
+                ux = u[0][:, 1:31, :]
+                ex = np.broadcast_to(exact[None, :, None], ux.shape)
+                res[f"l2_rel_err_{total}"] = float(np.sqrt(((ux - ex) ** 2).sum() / (ex ** 2).sum()))
+            m1, _ = L.reduce()
+            res["mass_drift_rel"] = abs(m1 - m0) / m0
+            res["u_max_exact"] = float(g * 30 ** 2 / (8 * nu))
+            out[dtype] = res
+    print(json.dumps(out), flush=True)
+
+
+def run_vessel(args):
+    """Synthetic vessel tree 1024 x 512 x 512 (seed 161102446, root radius 24, ratio 0.79,
+    6 generations, angles 25-45 deg), inlet u = 0.05 at x = 0, outlets at the leaf tips and
+    box faces, tau 0.6, no body force, non-periodic: MFLUPS and bandwidth for FP64 and FP32
+    storage over 5000 steps."""
+    import torch
+    import __graft_entry__
+    from paper_1611_02445_gb300 import inputs as I
+    from paper_1611_02445_gb300 import lbm
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    nt = I.vessel_tree()
+    peaks, _ = load_peaks()
+    out = {"workload": "vessel tree 1024x512x512, seed 161102446, tau 0.6, u_in 0.05, 4^3 tiles",
+           "fluid_fraction": float(np.count_nonzero(nt) / nt.size)}
+    for dtype in ("f64", "f32"):
+        with lbm.Lattice(nt, dtype, 0, stream) as L:
+            L.set_params(0.6, None, None, (0.05, 0.0, 0.0), 1.0)
+            L.init_equilibrium()
+            L.step(args.warmup)
+            ms = _timed_steps(L, 5000, stream)
+            info = L.info()
+            mass, _ = L.reduce()
+            n = info["n_nonsolid"]
+            mfl = n * 5000 / (ms * 1e-3) / 1e6
+            gbs = mfl * 1e6 * 2 * 19 * BYTES_PER_VALUE[dtype] / 1e9
+            out[dtype] = {"mflups": mfl, "ms_per_step": ms / 5000, "n_nonsolid": n, "n_tiles": info["n_tiles"],
+                          "eta_t": info["eta_t"], "algorithmic_gbs": gbs, "frac_of_measured_hbm": gbs / peaks["hbm_gbs"],
+                          "mass_after": mass}
+    print(json.dumps(out), flush=True)
+
+
+def run_precision(args):
+    """Precision sweep: sphere pack 512^3 (radius 8, porosity 0.35, seed 161102447), tau 0.7,
+    g_x 1e-5, periodic; FP64 vs FP32 vs FP16-shifted storage after args.steps steps (20 000
+    for steady state): velocity error relative to u_max and permeability k = nu <u_x> / g_x
+    (box average, solids counted as 0), against the FP64 run. On the 128^3 crop the same runs
+    are compared with the FP64 oracle after 2000 steps."""
+    import torch
+    import __graft_entry__
+    from oracle import oracle as O
+    from paper_1611_02445_gb300 import inputs as I
+    from paper_1611_02445_gb300 import lbm
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    tau, g = 0.7, (1e-5, 0.0, 0.0)
+    nu = (tau - 0.5) / 3.0
+
+    def run(nt, dtype, steps):
+        with lbm.Lattice(nt, dtype, 0b111, stream) as L:
+            L.set_params(tau, g)
+            L.init_equilibrium()
+            ms = _timed_steps(L, steps, stream)
+            rho, u = L.macroscopic()
+            return u, L.info()["n_nonsolid"] * steps / (ms * 1e-3) / 1e6
+
+    def compare(u, ref, solid):
+        umax = float(np.abs(ref[0]).max())
+        du = np.abs(u - ref)
+        return {"max_err_over_umax": float(du.max() / umax),
+                "l2_rel_err": float(np.sqrt((du ** 2).sum() / (ref ** 2).sum())),
+                "perm_rel_err": float(abs(u[0].mean() - ref[0].mean()) / abs(ref[0].mean())),
+                "u_max": umax}
+
+    out = {"workload": f"precision sweep: sphere pack 512^3 (seed 161102447), tau 0.7, g_x 1e-5, {args.steps} steps"}
+    nt = I.sphere_pack(512, 8.0, 0.35, I.SEED_POROUS_512)
+    u64, m64 = run(nt, "f64", args.steps)
+    out["f64"] = {"mflups": m64, "permeability": float(nu * u64[0].mean() / g[0])}
+    for dt in ("f32", "f16s"):
+        u, m = run(nt, dt, args.steps)
+        out[dt] = dict(compare(u, u64, nt == 0), mflups=m, speedup_vs_f64=m / m64)
+        del u
+    del u64
+    crop = I.crop(nt, 128)
+    steps_c = 2000
+    fo = O.run(O.init(crop), crop, steps_c, 0b111, tau, g, nthreads=os.cpu_count() or 1)
+    _, uo = O.macroscopic(fo, crop, g)
+    out["crop128_vs_oracle_2000_steps"] = {dt: compare(run(crop, dt, steps_c)[0], uo, crop == 0)
+                                           for dt in ("f64", "f64n", "f32", "f16s")}
+    print(json.dumps(out), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -221,6 +355,8 @@ def main():
                     help="the fused step, or one of the paper's calibration kernels (propagation "
                          "only, read/write only)")
     ap.add_argument("--adjoint", action="store_true", help="run the adjoint workload instead")
+    ap.add_argument("--workload", default="porous", choices=["porous", "poiseuille", "vessel", "precision"],
+                    help="porous is the benchmark line; the others print their own JSON line")
     ap.add_argument("--adj-steps", type=int, default=2000)
     ap.add_argument("--size", type=int, default=256,
                     help="edge of the cubic sphere pack (256 is the benchmark workload; smaller "
@@ -229,6 +365,9 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.adjoint:
         run_adjoint_workload(args)
+        return
+    if args.workload != "porous":
+        {"poiseuille": run_poiseuille, "vessel": run_vessel, "precision": run_precision}[args.workload](args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -62,7 +62,44 @@ cudaError_t dev_alloc(T** p, size_t count) {
     return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
+void drop_graphs(lbm_ctx* c) {
+    for (int i = 0; i < 2; i++)
+        if (c->graph[i]) {
+            cudaGraphExecDestroy(c->graph[i]);
+            c->graph[i] = nullptr;
+        }
+}
+
+// Capture GRAPH_STEPS steps starting from copy `start` on a private stream (the legacy
+// default stream cannot be captured); the graph is then launched on the context stream.
+cudaError_t build_graph(lbm_ctx* c, int start) {
+    cudaError_t e = lbm::prepare_step(c);
+    if (e != cudaSuccess) return e;
+    cudaStream_t cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return e;
+    cudaStream_t saved = c->stream;
+    c->stream = cap;
+    cudaGraph_t g = nullptr;
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        int cur = start;
+        for (int k = 0; k < lbm::GRAPH_STEPS && e == cudaSuccess; k++) {
+            e = lbm::launch_step(c, c->f[cur], c->f[1 - cur]);
+            cur ^= 1;
+        }
+        cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        if (e == cudaSuccess) e = e2;
+    }
+    c->stream = saved;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph[start], g, 0);
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    return e;
+}
+
 void free_all(lbm_ctx* c) {
+    drop_graphs(c);
     void* bufs[] = {c->tile_map, c->non_empty, c->nbr,    c->smask,  c->tflags, c->ntype,    c->nword,
                     c->groups,   c->fword,     c->fidx,   c->gfield, c->gfield_c, c->f[0], c->f[1],
                     c->partials, c->d_out};
@@ -365,6 +402,7 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
     }
     c->p.rho_out = rho_out;
     c->p.gfield = c->gfield;
+    drop_graphs(c);   // captured launches hold the old parameters
     c->p.dfc = lbm::make_df_const(c->p.omega, c->p.beta, c->p.g[1], c->p.g[2]);
     c->p.omega_f = (float)c->p.omega;
     c->p.beta_f = (float)c->p.beta;
@@ -392,7 +430,16 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
     LBM_CHECK_CTX(c);
     if (n < 0) return fail(c, LBM_EINVAL, "n must be >= 0");
     if (!c->state_set || !c->params_set) return fail(c, LBM_ESTATE, "set parameters and a state before stepping");
-    for (int k = 0; k < n; k++) {
+    int k = 0;
+    if (c->use_graphs && c->n_groups > 0 && n >= lbm::GRAPH_STEPS) {
+        // launch-bound small problems: replay a captured sequence of steps
+        for (; k + lbm::GRAPH_STEPS <= n; k += lbm::GRAPH_STEPS) {
+            if (!c->graph[c->cur]) LBM_CUDA(c, build_graph(c, c->cur));
+            LBM_CUDA(c, cudaGraphLaunch(c->graph[c->cur], c->stream));
+            // GRAPH_STEPS is even: the current copy is unchanged
+        }
+    }
+    for (; k < n; k++) {
         LBM_CUDA(c, lbm::launch_step(c, c->f[c->cur], c->f[1 - c->cur]));
         c->cur ^= 1;
     }

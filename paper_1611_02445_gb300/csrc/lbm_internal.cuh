@@ -45,6 +45,7 @@ constexpr int WORD_TYPE_SHIFT = 20;
 constexpr int WORD_LT_SHIFT = 22;      // compact words: tile within the group (3 bits)
 constexpr int WORD_SLOT_SHIFT = 25;    // compact words: slot in the tile (6 bits)
 constexpr int GROUP_MAX_TILES = 8;
+constexpr int GRAPH_STEPS = 16;
 // kernel kinds: the fused step and the paper's two calibration kernels (Sec. 4.1)
 constexpr int STEP_FULL = 0;        // gather, collide, store
 constexpr int STEP_PROPAGATE = 1;   // gather with bounce-back and store ("propagation only")
@@ -150,6 +151,9 @@ struct lbm_ctx {
     double* d_out = nullptr;
     int n_partials = 0;
     uint64_t geometry_hash = 0;
+    // CUDA graphs of GRAPH_STEPS consecutive steps, one per starting copy (0 or 1)
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool use_graphs = true;
     lbm_status sticky = LBM_OK;
     std::string err;
 };
@@ -167,6 +171,7 @@ cudaError_t launch_node_words(lbm_ctx* c);
 cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]);
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B);
 cudaError_t launch_step_kind(lbm_ctx* c, int kind, const void* A, void* B);
+cudaError_t prepare_step(lbm_ctx* c);
 cudaError_t launch_reduce(lbm_ctx* c, double* d_out);
 cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64);
 cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* d_out);

@@ -353,6 +353,20 @@ static cudaError_t launch_step_mode(lbm_ctx* c, const void* A, void* B) {
 
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B) { return launch_step_kind(c, STEP_FULL, A, B); }
 
+// One-time kernel attributes and occupancy query of the fused step, done outside any
+// stream capture.
+cudaError_t prepare_step(lbm_ctx* c) {
+    switch (c->dtype) {
+        case LBM_F64:
+            if (c->native64) step_grid<LBM_F64, true, STEP_FULL>(1);
+            else step_grid<LBM_F64, false, STEP_FULL>(1);
+            break;
+        case LBM_F32: step_grid<LBM_F32, false, STEP_FULL>(1); break;
+        default: step_grid<LBM_F16S, false, STEP_FULL>(1);
+    }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_step_kind(lbm_ctx* c, int kind, const void* A, void* B) {
     if (c->n_groups == 0) return cudaSuccess;
     switch (kind) {

@@ -326,3 +326,20 @@ def test_read_write_only_kernel_is_identity(dtype):
         L.step_kernel(lbm.KERNEL_RW, 5)
         fg = L.get_f()
     assert np.array_equal(fg, f_in, equal_nan=True)
+
+
+def test_graph_replay_matches_single_launches():
+    """lbm_step(n) replays a captured graph of 16 steps; the result equals n single steps."""
+    nt = I.random_box(12, 8, 16, p_solid=0.3, seed=41)
+    f0 = I.random_populations(nt, 0.05, seed=42)
+    outs = []
+    for chunk in (1, 37):
+        with lbm.Lattice(nt, "f64", 0b111) as L:
+            L.set_params(0.8, (1e-5, 0, 0))
+            L.set_f(f0)
+            for _ in range(37 // chunk):
+                L.step(chunk)
+            L.set_params(0.75, (1e-5, 0, 0))   # a parameter change drops the graphs
+            L.step(33)
+            outs.append(L.get_f())
+    assert np.array_equal(outs[0], outs[1], equal_nan=True)
