@@ -33,10 +33,12 @@ sys.path.insert(0, ROOT)
 METRIC = "MFLUPS (10^6 non-solid node updates per second) of the fused D3Q19 BGK sparse-tile step"
 WORKLOAD = ("porous sphere pack 256^3, radius 8, porosity 0.35, seed 161102445, D3Q19 BGK, "
             "tau 0.7, g_x 1e-5 (Guo), periodic, 4^3 tiles, all-solid tiles skipped")
-BYTES_PER_VALUE = {"f64": 8, "f64n": 8, "f32": 4, "f16s": 2}
+BYTES_PER_VALUE = {"f64": 8, "f64n": 8, "f32": 4, "f16s": 2, "f16sr": 2}
 DTYPE_NAME = {"f64": "f64 storage; FP64 moments and update, double-float (2xFP32) equilibrium and forcing",
               "f64n": "f64 storage, FP64 arithmetic throughout",
-              "f32": "f32", "f16s": "f16 (f - w shifted storage), f32 arithmetic"}
+              "f32": "f32 (f - w shifted storage), f32 arithmetic",
+              "f16s": "f16 (f - w shifted storage), f32 arithmetic",
+              "f16sr": "f16 (f - w shifted storage, stochastic rounding), f32 arithmetic"}
 
 
 def load_peaks():
@@ -221,10 +223,11 @@ def _timed_steps(L, n, stream):
 
 
 def run_poiseuille(args):
-    """Plane Poiseuille 32^3 (walls y = 0, 31; periodic x, z; tau 0.8; g_x 1e-6), FP64:
-    MFLUPS over 1000 steps (CUDA-graph replay; the problem is launch-bound), then the error
-    of u_x against g/(2 nu) (y - 1/2)(30.5 - y) at 1000 steps (start-up, not steady) and
-    at 12 000 steps, and the relative mass drift."""
+    """Plane Poiseuille 32^3 (walls y = 0, 31; periodic x, z; tau 0.8; g_x 1e-6) for every
+    storage format: MFLUPS over 1000 steps (CUDA-graph replay; the problem is launch-bound),
+    the error of u_x against g/(2 nu) (y - 1/2)(30.5 - y) at 1000 steps (start-up, not
+    steady) and at 12 000 steps, the relative mass drift, and, for the other formats, the
+    velocity error against the FP64 run at 12 000 steps."""
     import torch
     import __graft_entry__
     from paper_1611_02445_gb300 import inputs as I
@@ -236,8 +239,9 @@ def run_poiseuille(args):
     nu = (tau - 0.5) / 3.0
     y = np.arange(1, 31, dtype=np.float64)
     exact = g / (2 * nu) * (y - 0.5) * (30.5 - y)
-    out = {"workload": "plane Poiseuille 32^3, walls y=0,31, periodic x,z, tau 0.8, g_x 1e-6, FP64 storage"}
-    for dtype in ("f64", "f64n"):
+    out = {"workload": "plane Poiseuille 32^3, walls y=0,31, periodic x,z, tau 0.8, g_x 1e-6"}
+    u_end = {}
+    for dtype in ("f64", "f64n", "f32", "f16s", "f16sr"):
         with lbm.Lattice(nt, dtype, 0b101, stream) as L:
             L.set_params(tau, (g, 0.0, 0.0))
             L.init_equilibrium()
@@ -253,10 +257,17 @@ def run_poiseuille(args):
                 ux = u[0][:, 1:31, :]
                 ex = np.broadcast_to(exact[None, :, None], ux.shape)
                 res[f"l2_rel_err_{total}"] = float(np.sqrt(((ux - ex) ** 2).sum() / (ex ** 2).sum()))
+            u_end[dtype] = u[0][:, 1:31, :]
             m1, _ = L.reduce()
             res["mass_drift_rel"] = abs(m1 - m0) / m0
             res["u_max_exact"] = float(g * 30 ** 2 / (8 * nu))
             out[dtype] = res
+    ref = u_end["f64"]
+    umax = float(np.abs(ref).max())
+    for dtype in ("f64n", "f32", "f16s", "f16sr"):
+        du = np.abs(u_end[dtype] - ref)
+        out[dtype]["vs_f64_12000"] = {"max_err_over_umax": float(du.max() / umax),
+                                      "l2_rel_err": float(np.sqrt((du ** 2).sum() / (ref ** 2).sum()))}
     print(json.dumps(out), flush=True)
 
 
@@ -294,10 +305,11 @@ def run_vessel(args):
 
 def run_precision(args):
     """Precision sweep: sphere pack 512^3 (radius 8, porosity 0.35, seed 161102447), tau 0.7,
-    g_x 1e-5, periodic; FP64 vs FP32 vs FP16-shifted storage after args.steps steps (20 000
-    for steady state): velocity error relative to u_max and permeability k = nu <u_x> / g_x
-    (box average, solids counted as 0), against the FP64 run. On the 128^3 crop the same runs
-    are compared with the FP64 oracle after 2000 steps."""
+    g_x 1e-5, periodic; FP64 vs FP32 vs FP16-shifted storage (round to nearest and stochastic
+    rounding) after args.steps steps (20 000 for steady state): velocity error relative to
+    u_max and permeability k = nu <u_x> / g_x (box average, solids counted as 0), against
+    the FP64 run. On the 128^3 crop the same runs are compared with the FP64 oracle after
+    2000 steps."""
     import torch
     import __graft_entry__
     from oracle import oracle as O
@@ -328,7 +340,7 @@ def run_precision(args):
     nt = I.sphere_pack(512, 8.0, 0.35, I.SEED_POROUS_512)
     u64, m64 = run(nt, "f64", args.steps)
     out["f64"] = {"mflups": m64, "permeability": float(nu * u64[0].mean() / g[0])}
-    for dt in ("f32", "f16s"):
+    for dt in ("f32", "f16s", "f16sr"):
         u, m = run(nt, dt, args.steps)
         out[dt] = dict(compare(u, u64, nt == 0), mflups=m, speedup_vs_f64=m / m64)
         del u
@@ -338,7 +350,7 @@ def run_precision(args):
     fo = O.run(O.init(crop), crop, steps_c, 0b111, tau, g, nthreads=os.cpu_count() or 1)
     _, uo = O.macroscopic(fo, crop, g)
     out["crop128_vs_oracle_2000_steps"] = {dt: compare(run(crop, dt, steps_c)[0], uo, crop == 0)
-                                           for dt in ("f64", "f64n", "f32", "f16s")}
+                                           for dt in ("f64", "f64n", "f32", "f16s", "f16sr")}
     print(json.dumps(out), flush=True)
 
 
@@ -348,7 +360,7 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--dtype", default="f64", choices=["f64", "f64n", "f32", "f16s"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f64n", "f32", "f16s", "f16sr"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--kernel", default="full", choices=["full", "propagate", "rw"],

@@ -59,11 +59,23 @@ typedef enum {
  *                   about 46-48 bits), because GB300's FP64 pipe has 2 lanes per SM.
  *                   Agrees with FP64 arithmetic to ~1e-14 relative per step.
  *   LBM_F64_NATIVE  FP64 storage, every operation of the step in FP64.
- *   LBM_F32         FP32 storage, FP32 arithmetic.
+ *   LBM_F32         stores h_i = f_i - w_i as FP32 (the equilibrium-weight shift),
+ *                   FP32 arithmetic on h.
  *   LBM_F16S        stores h_i = (f_i - w_i) * 2^12 as IEEE binary16 (round to nearest
- *                   even), FP32 arithmetic.
+ *                   even), FP32 arithmetic on h.
+ *   LBM_F16S_SR     the LBM_F16S format, but the step rounds its stores stochastically:
+ *                   each result x (scaled h) is stored as the nearest binary16 to x + d,
+ *                   d uniform over one binary16 spacing of x (16-bit dither from a
+ *                   counter-based hash of the node, the direction and a step counter
+ *                   kept on the device), which rounds x up with probability equal to its
+ *                   distance from the lower neighbour. Increments smaller than half a
+ *                   spacing, which round-to-nearest drops, survive in expectation. Runs
+ *                   are reproducible: the counter restarts at lbm_init_equilibrium and is
+ *                   part of a saved state. lbm_adjoint returns LBM_EUNSUPPORTED for it.
+ * lbm_get_f and lbm_get_f_box return f = w_i + h_i in FP64, lbm_set_f rounds f - w_i
+ * to the stored format, and lbm_save_state copies the stored values as they are.
  * Inlet/outlet nodes use the FP64 arithmetic in both FP64 modes. */
-typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F64_NATIVE = 3 } lbm_dtype;
+typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F64_NATIVE = 3, LBM_F16S_SR = 4 } lbm_dtype;
 
 enum { LBM_SOLID = 0, LBM_FLUID = 1, LBM_INLET = 2, LBM_OUTLET = 3 };
 enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
@@ -160,7 +172,9 @@ lbm_status lbm_set_f(lbm_ctx* ctx, const double* f_dense);
  * Gradients accumulate in FP64; the adjoint arithmetic runs in the storage's arithmetic
  * precision (FP64 for LBM_F64, FP32 otherwise). Device memory: (ceil(T/ckpt_every) +
  * min(ckpt_every, T)) population copies plus two adjoint copies; if it cannot be
- * allocated the call returns LBM_ENOMEM before any work and the state is unchanged. */
+ * allocated the call returns LBM_ENOMEM before any work and the state is unchanged.
+ * A context of format LBM_F16S_SR returns LBM_EUNSUPPORTED (its recompute would not
+ * reproduce the forward's random rounding without storing the counter per segment). */
 lbm_status lbm_adjoint(lbm_ctx* ctx, int T, int ckpt_every, int plane_x, double* loss, double* dL_dg,
                        int dL_dg_on_device, double* dL_dtau);
 
@@ -172,7 +186,8 @@ lbm_status lbm_get_tiles(lbm_ctx* ctx, int32_t* tile_map, uint32_t* non_empty, i
 /* Sizes: n_tiles kept, n_nonsolid nodes, bytes of one population copy. Any may be NULL. */
 lbm_status lbm_get_info(lbm_ctx* ctx, int64_t* n_tiles, int64_t* n_nonsolid, int64_t* copy_bytes);
 
-/* Copy the current state (populations and step parity) to a host blob, or back.
+/* Copy the current state (the populations and, for LBM_F16S_SR, the step counter of the
+ * rounding) to a host blob, or back.
  * lbm_save_state with blob == NULL stores the size in *nbytes. The blob carries a
  * checksum and a hash of the geometry; loading a blob of another geometry, dtype or
  * with a bad checksum gives LBM_ESTATE. */

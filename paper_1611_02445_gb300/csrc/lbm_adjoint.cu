@@ -145,7 +145,7 @@ __device__ __forceinline__ R collide_adjoint(const R v[Q], const R lam[Q], int t
     }
     R D, rho;
     if (SHIFT) {
-        D = sum + R(WF_BIAS);
+        D = sum;
         rho = R(1) + D;
     } else {
         rho = sum;

@@ -102,7 +102,7 @@ void free_all(lbm_ctx* c) {
     drop_graphs(c);
     void* bufs[] = {c->tile_map, c->non_empty, c->nbr,    c->smask,  c->tflags, c->ntype,    c->nword,
                     c->groups,   c->fword,     c->fidx,   c->gfield, c->gfield_c, c->f[0], c->f[1],
-                    c->partials, c->d_out};
+                    c->partials, c->d_out, c->seed};
     for (void* b : bufs)
         if (b) cudaFree(b);
     c->tile_map = nullptr;
@@ -120,6 +120,7 @@ void free_all(lbm_ctx* c) {
     c->gfield = nullptr;
     c->partials = nullptr;
     c->d_out = nullptr;
+    c->seed = nullptr;
 }
 
 // Device-side check that every neighbour entry is -1 or a valid rank.
@@ -149,6 +150,8 @@ struct StateHeader {
     uint64_t geometry_hash;
     uint64_t payload_bytes;
     uint64_t payload_hash;
+    uint32_t rng_step;   // step counter of the stochastic rounding (LBM_F16S_SR), else 0
+    uint32_t reserved;
 };
 
 lbm_status geometry_hash(lbm_ctx* c, uint64_t* out) {
@@ -188,10 +191,13 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     if (!node_type) return fail(nullptr, LBM_EINVAL, "node_type is NULL");
     if (tile != lbm::TILE) return fail(nullptr, LBM_EUNSUPPORTED, "only 4x4x4 tiles are supported");
     if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "dimensions must be >= 1");
-    if (dtype != LBM_F64 && dtype != LBM_F32 && dtype != LBM_F16S && dtype != LBM_F64_NATIVE)
+    if (dtype != LBM_F64 && dtype != LBM_F32 && dtype != LBM_F16S && dtype != LBM_F64_NATIVE &&
+        dtype != LBM_F16S_SR)
         return fail(nullptr, LBM_EINVAL, "unknown dtype");
     const bool native64 = dtype == LBM_F64_NATIVE;
     if (native64) dtype = LBM_F64;
+    const bool sr = dtype == LBM_F16S_SR;
+    if (sr) dtype = LBM_F16S;
     if (periodic & ~7u) return fail(nullptr, LBM_EINVAL, "periodic mask has bits other than x, y, z");
     const int dims[3] = {nx, ny, nz};
     for (int a = 0; a < 3; a++)
@@ -208,6 +214,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     c->periodic = periodic;
     c->dtype = dtype;
     c->native64 = native64;
+    c->sr = sr;
     c->stream = static_cast<cudaStream_t>(stream);
 
     uint8_t* d_nt = nullptr;
@@ -277,6 +284,10 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     LBM_CREATE_CUDA(dev_alloc(&c->d_out, 8));
     LBM_CREATE_CUDA(cudaMalloc(&c->f[0], std::max<size_t>(copy_bytes, 16)));
     LBM_CREATE_CUDA(cudaMalloc(&c->f[1], std::max<size_t>(copy_bytes, 16)));
+    if (sr) {
+        LBM_CREATE_CUDA(dev_alloc(&c->seed, 2));
+        LBM_CREATE_CUDA(cudaMemsetAsync(c->seed, 0, 2 * sizeof(uint32_t), c->stream));
+    }
     LBM_CREATE_CUDA(lbm::launch_tile_meta(c, d_nt));
     unsigned long long nonsolid = 0;
     LBM_CREATE_CUDA(cudaMemcpyAsync(&nonsolid, c->d_out, sizeof(nonsolid), cudaMemcpyDeviceToHost, c->stream));
@@ -421,6 +432,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx* c, double rho0, const double* u0) {
     if (!(std::isfinite(rho0) && rho0 > 0.0) || !finite3(u0)) return fail(c, LBM_EINVAL, "rho0 must be > 0, u0 finite");
     const double z[3] = {0.0, 0.0, 0.0};
     if (c->n_tiles > 0) LBM_CUDA(c, lbm::launch_init(c, rho0, u0 ? u0 : z));
+    if (c->seed) LBM_CUDA(c, cudaMemsetAsync(c->seed, 0, 2 * sizeof(uint32_t), c->stream));
     c->cur = 0;
     c->state_set = true;
     return LBM_OK;
@@ -549,6 +561,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int T, int ckpt_every, int plane_x, double* l
     if (T < 1 || ckpt_every < 1 || !loss) return fail(c, LBM_EINVAL, "T >= 1, ckpt_every >= 1 and loss are required");
     if (plane_x < 0 || plane_x >= c->nx) return fail(c, LBM_EINVAL, "plane_x outside the box");
     if (!c->state_set || !c->params_set) return fail(c, LBM_ESTATE, "set parameters and a state first");
+    if (c->sr) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint does not support stochastic rounding (LBM_F16S_SR)");
     if (c->n_tiles == 0) {
         *loss = 0.0;
         if (dL_dtau) *dL_dtau = 0.0;
@@ -596,7 +609,7 @@ lbm_status lbm_save_state(lbm_ctx* c, void* blob, size_t* nbytes) {
     if (!c->state_set) return fail(c, LBM_ESTATE, "no state");
     StateHeader h{};
     std::memcpy(h.magic, "LBMGB300", 8);
-    h.version = 1;
+    h.version = 2;
     h.dtype = c->dtype;
     h.nx = c->nx; h.ny = c->ny; h.nz = c->nz;
     h.periodic = c->periodic;
@@ -605,10 +618,9 @@ lbm_status lbm_save_state(lbm_ctx* c, void* blob, size_t* nbytes) {
     if (st != LBM_OK) return st;
     h.payload_bytes = payload;
     char* dst = static_cast<char*>(blob) + sizeof(StateHeader);
-    if (payload > 0) {
-        LBM_CUDA(c, cudaMemcpyAsync(dst, c->f[c->cur], payload, cudaMemcpyDeviceToHost, c->stream));
-        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
+    if (c->seed) LBM_CUDA(c, cudaMemcpyAsync(&h.rng_step, c->seed + c->cur, 4, cudaMemcpyDeviceToHost, c->stream));
+    if (payload > 0) LBM_CUDA(c, cudaMemcpyAsync(dst, c->f[c->cur], payload, cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     h.payload_hash = fnv1a(dst, payload);
     std::memcpy(blob, &h, sizeof(h));
     *nbytes = total;
@@ -621,7 +633,7 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* blob, size_t nbytes) {
     StateHeader h;
     std::memcpy(&h, blob, sizeof(h));
     const size_t payload = (size_t)c->n_tiles * lbm::Q * lbm::SLOTS * lbm::dtype_size(c->dtype);
-    if (std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) return fail(c, LBM_ESTATE, "not a state blob");
+    if (std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2) return fail(c, LBM_ESTATE, "not a state blob");
     if (h.dtype != c->dtype || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.periodic != c->periodic ||
         h.n_tiles != c->n_tiles || h.payload_bytes != payload || nbytes < sizeof(h) + payload)
         return fail(c, LBM_ESTATE, "state blob is for another geometry or dtype");
@@ -631,10 +643,9 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* blob, size_t nbytes) {
     lbm_status st = geometry_hash(c, &gh);
     if (st != LBM_OK) return st;
     if (gh != h.geometry_hash) return fail(c, LBM_ESTATE, "state blob geometry hash mismatch");
-    if (payload > 0) {
-        LBM_CUDA(c, cudaMemcpyAsync(c->f[c->cur], src, payload, cudaMemcpyHostToDevice, c->stream));
-        LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-    }
+    if (payload > 0) LBM_CUDA(c, cudaMemcpyAsync(c->f[c->cur], src, payload, cudaMemcpyHostToDevice, c->stream));
+    if (c->seed) LBM_CUDA(c, cudaMemcpyAsync(c->seed + c->cur, &h.rng_step, 4, cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->state_set = true;
     return LBM_OK;
 }

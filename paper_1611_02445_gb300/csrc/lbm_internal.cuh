@@ -91,7 +91,7 @@ template <> struct Store<LBM_F64> {
 template <> struct Store<LBM_F32> {
     using T = float;
     using R = float;
-    static constexpr bool SHIFT = true;    // arithmetic on h = f - w, stored as f
+    static constexpr bool SHIFT = true;    // arithmetic and storage on h = f - w
 };
 template <> struct Store<LBM_F16S> {
     using T = __half;
@@ -125,6 +125,8 @@ struct lbm_ctx {
     unsigned periodic = 0;
     int dtype = LBM_F64;        // storage format (LBM_F64, LBM_F32, LBM_F16S)
     bool native64 = false;      // LBM_F64_NATIVE: FP64 arithmetic throughout
+    bool sr = false;            // LBM_F16S_SR: stochastic rounding of the step's stores
+    uint32_t* seed = nullptr;   // step counters of the rounding hash, one per copy
     int64_t n_tiles = 0, n_nonsolid = 0;
     cudaStream_t stream = nullptr;
     int32_t* tile_map = nullptr;

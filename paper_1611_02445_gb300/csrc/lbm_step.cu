@@ -49,6 +49,39 @@ __device__ __forceinline__ void bgk_pair(R& a, R& b, R w, R cu, R cF, R D, R rho
     b = om1 * b + (omega * (E - O) + (Se - So));
 }
 
+// The same update on h = f - w written with j' = rho u = j + F/2 (SHIFT = true):
+//   h^eq_i = w (D + 3 c.j' + (4.5 (c.j')^2 - 1.5 |j'|^2) / rho),  D = rho - 1.
+// The odd part 3 w c.j' then carries the momentum exactly as summed, instead of through
+// the rounded u = j' / rho; the second-order part and the Guo term use 1 / rho.
+//
+// FP32 lattice constants: the collision conserves mass and momentum through two lattice
+// identities, sum_i w_i = 1 (for w_i D) and sum_i 3 w_i c_ix^2 = 1 (for the odd part
+// 3 w_i c_i.j'). With 1/3, 1/18, 1/36 rounded to FP32 the second is off by 3.0e-8, so
+// every collision would add 3e-8 omega j' of momentum: a force proportional to the local
+// velocity, a relative velocity error of ~3e-8 omega u / F in a slow steady flow. These
+// constants satisfy both identities exactly in binary arithmetic (w1 = 14913080 2^-28,
+// w2 = w1 / 2, w0 = 1 - 6 w1 - 12 w2 = 11184812 2^-25; a_k replaces 3 w_k in the odd
+// part with 2 a1 + 8 a2 = 1: a1 = 11184810 2^-26, a2 = 11184811 2^-27) and differ from
+// the exact weights by less than 2e-7 relative.
+constexpr float W0S = 11184812.0f / 33554432.0f;
+constexpr float W1S = 14913080.0f / 268435456.0f;
+constexpr float W2S = 7456540.0f / 268435456.0f;
+constexpr float A1S = 11184810.0f / 67108864.0f;
+constexpr float A2S = 11184811.0f / 134217728.0f;
+
+template <typename R>
+__device__ __forceinline__ void bgk_pair_j(R& a, R& b, R w, R aw, R cj, R cF, R D, R inv_rho, R jj15, R uF3,
+                                           R omega, R om1, R beta) {
+    const R cu = cj * inv_rho;
+    const R E = w * D + w * ((R(4.5) * cj * cj - jj15) * inv_rho);
+    const R O = aw * cj;
+    const R bw = beta * w;
+    const R Se = bw * (R(9) * cu * cF - uF3);
+    const R So = (beta * aw) * cF;
+    a = om1 * a + (omega * (E + O) + (Se + So));
+    b = om1 * b + (omega * (E - O) + (Se - So));
+}
+
 // Equilibrium of one direction pair: v_i = w (D + rho (3 cu + 4.5 cu^2 - 1.5 u.u)).
 template <typename R>
 __device__ __forceinline__ void eq_pair(R& a, R& b, R w, R cu, R D, R rho, R uu15) {
@@ -72,18 +105,34 @@ __device__ __forceinline__ void collide(R v[Q], int type, const StepParams& p, R
     const R jz = ((d56 + d1114) - d1213) + (d1518 - d1617);
     R D, rho;
     if (SHIFT) {
-        D = sum + R(WF_BIAS);
+        D = sum;
         rho = R(1) + D;
     } else {
         rho = sum;
         D = sum;
     }
     const R inv_rho = R(1) / rho;
-    const R ux = (jx + R(0.5) * Fx) * inv_rho;
-    const R uy = (jy + R(0.5) * Fy) * inv_rho;
-    const R uz = (jz + R(0.5) * Fz) * inv_rho;
+    const R Jx = jx + R(0.5) * Fx, Jy = jy + R(0.5) * Fy, Jz = jz + R(0.5) * Fz;
+    const R ux = Jx * inv_rho;
+    const R uy = Jy * inv_rho;
+    const R uz = Jz * inv_rho;
     const R w0 = R(wgt(0)), w1 = R(wgt(1)), w2 = R(wgt(7));
-    if (type == LBM_FLUID) {
+    if (SHIFT && type == LBM_FLUID) {
+        const R omega = par<R>(p.omega, p.omega_f), om1 = R(1) - omega, beta = par<R>(p.beta, p.beta_f);
+        const R jj15 = R(1.5) * (Jx * Jx + Jy * Jy + Jz * Jz);
+        const R uF3 = R(3) * (ux * Fx + uy * Fy + uz * Fz);
+        const R s0 = R(W0S), s1 = R(W1S), s2 = R(W2S), a1 = R(A1S), a2 = R(A2S);
+        v[0] = om1 * v[0] + (omega * (s0 * D - s0 * (jj15 * inv_rho)) - (beta * s0) * uF3);
+        bgk_pair_j(v[1], v[3], s1, a1, Jx, Fx, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[2], v[4], s1, a1, Jy, Fy, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[5], v[6], s1, a1, Jz, Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[7], v[9], s2, a2, Jx + Jy, Fx + Fy, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[8], v[10], s2, a2, Jy - Jx, Fy - Fx, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[11], v[14], s2, a2, Jx + Jz, Fx + Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[12], v[13], s2, a2, Jx - Jz, Fx - Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[15], v[18], s2, a2, Jy + Jz, Fy + Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[16], v[17], s2, a2, Jy - Jz, Fy - Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+    } else if (type == LBM_FLUID) {
         const R omega = par<R>(p.omega, p.omega_f), om1 = R(1) - omega, beta = par<R>(p.beta, p.beta_f);
         const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
         const R uF3 = R(3) * (ux * Fx + uy * Fy + uz * Fz);
@@ -220,10 +269,33 @@ __device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, in
     return odd;
 }
 
-template <int DT, bool NATIVE, int MODE>
+// ------------------------------------------------------------ stochastic rounding
+// MurmurHash3's 32-bit finaliser (A. Appleby, public domain): a bijective avalanche mix,
+// used as a counter-based generator keyed by (step counter, node, direction pair).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// binary16 nearest to x + d, d = (r - 32767.5) 2^-16 s uniform over one binary16 spacing
+// s of x (r: 16 random bits). For x in (lo, lo + s) this rounds up with probability
+// (x - lo) / s to 16 bits, i.e. stochastic rounding (the FP32 sum x + d is off by at most
+// 2^-14 s). s = 2^(e - 10) for |x| >= 2^-14 (e the exponent of x), 2^-24 below.
+__device__ __forceinline__ __half half_dithered(float x, uint32_t r) {
+    const uint32_t eb = __float_as_uint(x) & 0x7f800000u;
+    const uint32_t sb = max(eb, 113u << 23) - (26u << 23);   // s * 2^-16
+    const float d = __fmul_rn(__int2float_rn((int)r - 32767) - 0.5f, __uint_as_float(sb));
+    return __float2half_rn(__fadd_rn(x, d));
+}
+
+template <int DT, bool VAR, int MODE>
 __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, uint32_t odd,
                                               typename Store<DT>::T* __restrict__ B, const StepParams& p,
-                                              bool has_gf) {
+                                              bool has_gf, uint32_t key) {
     using R = typename Store<DT>::R;
     using T = typename Store<DT>::T;
     const int t = threadIdx.x;
@@ -249,7 +321,7 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     const R Fy = par<R>(p.g[1], p.g_f[1]), Fz = par<R>(p.g[2], p.g_f[2]);
     if constexpr (MODE != STEP_FULL) {
         // calibration kernels: no collision, the gathered values are stored as they are
-    } else if constexpr (DT == LBM_F64 && !NATIVE) {
+    } else if constexpr (DT == LBM_F64 && !VAR) {
         // FP64 storage: double-float collision for fluid nodes, FP64 for the closures
         if (type == LBM_FLUID) collide_df(v, (double)Fx, p.dfc);
         else collide<R, false>(v, type, p, Fx, Fy, Fz);
@@ -257,8 +329,19 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
         collide<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
     }
     const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
+    if constexpr (DT == LBM_F16S && VAR && MODE == STEP_FULL) {
+        // stochastic rounding: two 16-bit dithers per hash of (key, node, pair)
+        const uint32_t node = fmix32(key ^ (uint32_t)((h.x + lt) * SLOTS + s));
 #pragma unroll
-    for (int i = 0; i < Q; i++) B[own + i * SLOTS + s] = to_store<DT>(v[i], i);
+        for (int i = 0; i < Q; i += 2) {
+            const uint32_t r = fmix32(node + (uint32_t)(i >> 1) * 0x9e3779b9u);
+            B[own + i * SLOTS + s] = half_dithered(v[i] * F16_SCALE, r & 0xffffu);
+            if (i + 1 < Q) B[own + (i + 1) * SLOTS + s] = half_dithered(v[i + 1] * F16_SCALE, r >> 16);
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < Q; i++) B[own + i * SLOTS + s] = to_store<DT>(v[i], i);
+    }
 }
 
 // Resident CTAs per SM the kernel is compiled for: shared memory allows 4 CTAs of the
@@ -266,15 +349,24 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
 template <int DT> struct StepOcc { static constexpr int CTAS = 4; };
 template <> struct StepOcc<LBM_F64> { static constexpr int CTAS = 2; };
 
-template <int DT, bool NATIVE, int MODE>
+template <int DT, bool VAR, int MODE>
 __global__ void __launch_bounds__(STEP_THREADS, StepOcc<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
-       const void* __restrict__ gfield_c, int64_t n_groups, StepParams p) {
+       const void* __restrict__ gfield_c, int64_t n_groups, StepParams p, const uint32_t* __restrict__ seed_in,
+       uint32_t* __restrict__ seed_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<DT>& sm = *reinterpret_cast<StepSmem<DT>*>(smem_raw);
     const int64_t G = gridDim.x;
     const int64_t g0 = blockIdx.x;
+    uint32_t key = 0;
+    if (DT == LBM_F16S && VAR) {
+        // step counter of the rounding hash: read from this launch's copy, advanced into
+        // the other copy's, which no thread of this launch reads
+        const uint32_t t = *seed_in;
+        if (blockIdx.x == 0 && threadIdx.x == 0) *seed_out = t + 1u;
+        key = fmix32(t * 0x9e3779b9u + 0x7f4a7c15u);
+    }
     if (g0 >= n_groups) return;
     const bool has_gf = gfield_c != nullptr;
     // prologue: headers of groups 0..2, meta of groups 0..1, gathers of group 0
@@ -309,34 +401,39 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         cp_async_commit();
         // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
         cp_async_wait<3>();
-        compute_store<DT, NATIVE, MODE>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], odd_cur, B, p, has_gf);
+        compute_store<DT, VAR, MODE>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], odd_cur, B, p, has_gf, key);
         odd_cur = odd_next;
     }
     cp_async_wait<0>();
 }
 
-template <int DT, bool NATIVE, int MODE>
+template <int DT, bool VAR, int MODE>
 static int step_grid(int64_t n_groups) {
     static int per_sm = -1, n_sm = 0;
     if (per_sm < 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_step<DT, NATIVE, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step<DT, VAR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, NATIVE, MODE>, STEP_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, VAR, MODE>, STEP_THREADS,
                                                       sizeof(StepSmem<DT>));
         if (per_sm < 1) per_sm = 1;
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)per_sm * n_sm));
 }
 
-template <int DT, bool NATIVE, int MODE>
+template <int DT, bool VAR, int MODE>
 static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
-    const int grid = step_grid<DT, NATIVE, MODE>(c->n_groups);
-    k_step<DT, NATIVE, MODE><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
-        (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p);
+    const int grid = step_grid<DT, VAR, MODE>(c->n_groups);
+    // the copy read decides which counter is read and which is advanced
+    const int from = A == c->f[0] ? 0 : 1;
+    const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
+    uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
+    k_step<DT, VAR, MODE><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
+        (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
+        seed_in, seed_out);
     return cudaGetLastError();
 }
 
@@ -347,7 +444,9 @@ static cudaError_t launch_step_mode(lbm_ctx* c, const void* A, void* B) {
             return c->native64 ? launch_step_dt<LBM_F64, true, MODE>(c, A, B)
                                : launch_step_dt<LBM_F64, false, MODE>(c, A, B);
         case LBM_F32: return launch_step_dt<LBM_F32, false, MODE>(c, A, B);
-        default: return launch_step_dt<LBM_F16S, false, MODE>(c, A, B);
+        default:
+            return c->sr ? launch_step_dt<LBM_F16S, true, MODE>(c, A, B)
+                         : launch_step_dt<LBM_F16S, false, MODE>(c, A, B);
     }
 }
 
@@ -362,7 +461,9 @@ cudaError_t prepare_step(lbm_ctx* c) {
             else step_grid<LBM_F64, false, STEP_FULL>(1);
             break;
         case LBM_F32: step_grid<LBM_F32, false, STEP_FULL>(1); break;
-        default: step_grid<LBM_F16S, false, STEP_FULL>(1);
+        default:
+            if (c->sr) step_grid<LBM_F16S, true, STEP_FULL>(1);
+            else step_grid<LBM_F16S, false, STEP_FULL>(1);
     }
     return cudaGetLastError();
 }

@@ -16,8 +16,8 @@ import numpy as np
 
 from . import build as _build
 
-LBM_F64, LBM_F32, LBM_F16S, LBM_F64_NATIVE = 0, 1, 2, 3
-DTYPES = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "f64n": LBM_F64_NATIVE}
+LBM_F64, LBM_F32, LBM_F16S, LBM_F64_NATIVE, LBM_F16S_SR = 0, 1, 2, 3, 4
+DTYPES = {"f64": LBM_F64, "f32": LBM_F32, "f16s": LBM_F16S, "f64n": LBM_F64_NATIVE, "f16sr": LBM_F16S_SR}
 SOLID, FLUID, INLET, OUTLET = 0, 1, 2, 3
 PERIODIC_X, PERIODIC_Y, PERIODIC_Z = 1, 2, 4
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSUPPORTED",

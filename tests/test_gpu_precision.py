@@ -1,0 +1,160 @@
+"""Reduced-precision storage on the GPU, through the C ABI: what each format keeps of a
+small steady flow, and the properties of stochastic rounding (LBM_F16S_SR).
+
+Bars
+  - stochastic rounding is unbiased: a uniform force whose per-step increments lie below
+    half a binary16 spacing leaves a round-to-nearest state at rest (exactly) but builds
+    the momentum N F (n - 1/2) (Guo forcing, reported with the half-force shift) under
+    stochastic rounding, to within a few standard deviations of the rounding noise;
+  - runs are reproducible: the same steps give bit-identical states whether replayed from
+    CUDA graphs or launched one by one, and a saved state continues identically;
+  - plane Poiseuille (the 32^3 channel of the validation case, 12 000 steps): the
+    velocity error of each format against the FP64 run, relative to u_max, within the
+    bound stated per format.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1611_02445_gb300 import build as B
+from paper_1611_02445_gb300 import inputs as I
+from paper_1611_02445_gb300 import lbm
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    B.build()
+    lbm.load()
+
+
+def test_stochastic_rounding_keeps_sub_spacing_increments():
+    """16^3 periodic fluid box at rest, g_x = 1e-11, tau 0.8: the first post-collision h_1
+    is about 1.7e-12, 6.8e-9 after the 2^12 scale, below half the smallest binary16
+    spacing (2^-25 = 3.0e-8), so round-to-nearest stores 0 everywhere, every step. Under
+    stochastic rounding the momentum after n steps is N g (n - 1/2) in expectation; the
+    noise of one step is about sqrt(10 N) * 2^-24 / 2^12 * 0.5 ~ 4.6e-10, so after 64
+    steps its standard deviation is ~3.7e-9 against 2.6e-6 expected (0.15 %)."""
+    nt = I.dense_box(16, 16, 16)
+    N = nt.size
+    g, n = 1e-11, 64
+    out = {}
+    for dtype in ("f16s", "f16sr"):
+        with lbm.Lattice(nt, dtype, 0b111) as L:
+            L.set_params(0.8, (g, 0.0, 0.0))
+            L.init_equilibrium()
+            L.step(n)
+            out[dtype] = (L.reduce(), L.get_f())
+    (m_rn, p_rn), f_rn = out["f16s"]
+    _, W, _ = O.lattice()
+    assert np.array_equal(f_rn, np.broadcast_to(W[:, None, None, None], f_rn.shape))
+    assert p_rn[0] == pytest.approx(-0.5 * N * g, rel=1e-12)
+    (m_sr, p_sr), _ = out["f16sr"]
+    expected = N * g * (n - 0.5)
+    print(f"momentum after {n} steps: RN {p_rn[0]:.4e}, SR {p_sr[0]:.4e}, expected {expected:.4e}")
+    assert abs(p_sr[0] - expected) <= 0.02 * expected
+    assert abs(p_sr[1]) <= 0.02 * expected and abs(p_sr[2]) <= 0.02 * expected
+
+
+def _run(nt, dtype, chunks, tau=0.8, g=(1e-5, 0.0, 0.0), periodic=0b111, f0=None):
+    with lbm.Lattice(nt, dtype, periodic) as L:
+        L.set_params(tau, g)
+        if f0 is None:
+            L.init_equilibrium()
+        else:
+            L.set_f(f0)
+        for c in chunks:
+            L.step(c)
+        return L.get_f()
+
+
+def test_stochastic_rounding_reproducible_graphs_and_single_launches():
+    nt = I.random_box(16, 12, 8, p_solid=0.3, seed=4)
+    a = _run(nt, "f16sr", [32])            # two graph replays
+    b = _run(nt, "f16sr", [15, 15, 2])     # single launches only
+    c = _run(nt, "f16sr", [16, 3, 13])     # mixed
+    assert np.array_equal(a, b, equal_nan=True)
+    assert np.array_equal(a, c, equal_nan=True)
+    d = _run(nt, "f16s", [32])
+    assert not np.array_equal(a, d, equal_nan=True)
+
+
+def test_stochastic_rounding_state_roundtrip_and_restart():
+    nt = I.random_box(8, 8, 8, p_solid=0.2, seed=9)
+    with lbm.Lattice(nt, "f16sr", 0b111) as L:
+        L.set_params(0.8, (1e-5, 0.0, 0.0))
+        L.init_equilibrium()
+        L.step(20)
+        blob = L.save_state()
+        L.step(17)
+        f37 = L.get_f()
+        L.load_state(blob)
+        L.step(17)
+        assert np.array_equal(L.get_f(), f37, equal_nan=True)
+        L.init_equilibrium()      # restarts the counter
+        L.step(37)
+        assert np.array_equal(L.get_f(), f37, equal_nan=True)
+
+
+def test_stochastic_rounding_adjoint_unsupported():
+    nt = I.dense_box(8, 8, 8)
+    with lbm.Lattice(nt, "f16sr", 0b111) as L:
+        L.set_params(0.8)
+        L.init_equilibrium()
+        with pytest.raises(lbm.LBMError) as e:
+            L.adjoint(4, 2, 3)
+        assert e.value.status == 4
+
+
+# Bounds on max |u - u_f64| / u_max at 12 000 steps of the 32^3 channel. The channel is
+# uniform in x and z, so every node of a y-plane rounds alike and the storage rounding
+# acts as a coherent force: FP32 ~3e-5 (2^-24 of h_1 ~ 3 w u against g = 1e-6 a step).
+# Round-to-nearest FP16 stalls (the force increment is below half a spacing of h) and is
+# reported, not bounded; stochastic rounding keeps the increments.
+POISEUILLE_BOUNDS = {"f64n": 1e-9, "f32": 6e-5, "f16sr": 2e-3}
+
+
+def test_poiseuille_steady_state_per_format():
+    nt = I.poiseuille_channel(32, 32, 32)
+    u = {}
+    for dtype in ("f64", "f64n", "f32", "f16s", "f16sr"):
+        with lbm.Lattice(nt, dtype, 0b101) as L:
+            L.set_params(0.8, (1e-6, 0.0, 0.0))
+            L.init_equilibrium()
+            L.step(12000)
+            u[dtype] = L.macroscopic()[1][0][:, 1:31, :]
+    ref = u["f64"]
+    umax = np.abs(ref).max()
+    errs = {d: float(np.abs(u[d] - ref).max() / umax) for d in u if d != "f64"}
+    print("max |u - u_f64| / u_max:", errs)
+    for d, b in POISEUILLE_BOUNDS.items():
+        assert errs[d] <= b, (d, errs[d])
+
+
+# Bounds on a 64^3 periodic sphere pack (radius 8, porosity 0.35, the precision-sweep
+# recipe at a size the oracle runs in seconds) after 1000 steps against the oracle:
+# max |u - u_oracle| / u_max and the relative L2 error.
+CROP_BOUNDS = {"f64": (1e-9, 1e-10), "f32": (1e-5, 5e-6), "f16s": (5e-3, 1e-3), "f16sr": (5e-3, 1e-3)}
+
+
+def test_porous_crop_per_format_vs_oracle():
+    import os
+    nt = I.sphere_pack(64, 8.0, 0.35, I.SEED_POROUS_512)
+    tau, g, steps = 0.7, (1e-5, 0.0, 0.0), 1000
+    fo = O.run(O.init(nt), nt, steps, 0b111, tau, g, nthreads=os.cpu_count() or 1)
+    _, uo = O.macroscopic(fo, nt, g)
+    umax = np.abs(uo[0]).max()
+    for dtype, (bmax, bl2) in CROP_BOUNDS.items():
+        with lbm.Lattice(nt, dtype, 0b111) as L:
+            L.set_params(tau, g)
+            L.init_equilibrium()
+            L.step(steps)
+            u = L.macroscopic()[1]
+        du = np.abs(u - uo)
+        emax = du.max() / umax
+        el2 = np.sqrt((du ** 2).sum() / (uo ** 2).sum())
+        print(f"{dtype}: max {emax:.3e}, L2 {el2:.3e}")
+        assert emax <= bmax and el2 <= bl2, (dtype, emax, el2)
