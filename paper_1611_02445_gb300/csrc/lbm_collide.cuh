@@ -1,0 +1,175 @@
+// lbm_collide.cuh -- the local collision of one node (Eq. 2, 3, 7 with Guo forcing) in
+// the arithmetic of the FP64-native, FP32 and FP16 storage formats, and the stochastic
+// rounding of stores. Shared by the step kernels.
+#pragma once
+#include "lbm_internal.cuh"
+#include "lbm_store.cuh"
+
+namespace lbm {
+
+// LBGK + Guo update of one direction pair (i, inv(i)) with lattice velocity c = c_i.
+// Works on f (SHIFT = false, D = rho) or on h = f - w (SHIFT = true, D = rho - 1):
+//   f^eq_i - w_i (if shifted) = w (D + rho (3 cu + 4.5 cu^2 - 1.5 u.u))      (Eq. 3)
+//   S_i = beta w (3 (c - u).F + 9 (c.u)(c.F))                               (Guo)
+//   v*_i = (1 - omega) v_i + omega v^eq_i + S_i                              (Eq. 7)
+// split into the parts even (E, Se) and odd (O, So) in c.
+template <typename R>
+__device__ __forceinline__ void bgk_pair(R& a, R& b, R w, R cu, R cF, R D, R rho, R uu15, R uF3,
+                                         R omega, R om1, R beta) {
+    const R E = w * D + (w * rho) * (R(4.5) * cu * cu - uu15);
+    const R O = R(3) * (w * rho) * cu;
+    const R bw = beta * w;
+    const R Se = bw * (R(9) * cu * cF - uF3);
+    const R So = R(3) * bw * cF;
+    a = om1 * a + (omega * (E + O) + (Se + So));
+    b = om1 * b + (omega * (E - O) + (Se - So));
+}
+
+// The same update on h = f - w written with j' = rho u = j + F/2 (SHIFT = true):
+//   h^eq_i = w (D + 3 c.j' + (4.5 (c.j')^2 - 1.5 |j'|^2) / rho),  D = rho - 1.
+// The odd part 3 w c.j' then carries the momentum exactly as summed, instead of through
+// the rounded u = j' / rho; the second-order part and the Guo term use 1 / rho.
+//
+// FP32 lattice constants: the collision conserves mass and momentum through two lattice
+// identities, sum_i w_i = 1 (for w_i D) and sum_i 3 w_i c_ix^2 = 1 (for the odd part
+// 3 w_i c_i.j'). With 1/3, 1/18, 1/36 rounded to FP32 the second is off by 3.0e-8, so
+// every collision would add 3e-8 omega j' of momentum: a force proportional to the local
+// velocity, a relative velocity error of ~3e-8 omega u / F in a slow steady flow. These
+// constants satisfy both identities exactly in binary arithmetic (w1 = 14913080 2^-28,
+// w2 = w1 / 2, w0 = 1 - 6 w1 - 12 w2 = 11184812 2^-25; a_k replaces 3 w_k in the odd
+// part with 2 a1 + 8 a2 = 1: a1 = 11184810 2^-26, a2 = 11184811 2^-27) and differ from
+// the exact weights by less than 2e-7 relative.
+constexpr float W0S = 11184812.0f / 33554432.0f;
+constexpr float W1S = 14913080.0f / 268435456.0f;
+constexpr float W2S = 7456540.0f / 268435456.0f;
+constexpr float A1S = 11184810.0f / 67108864.0f;
+constexpr float A2S = 11184811.0f / 134217728.0f;
+
+template <typename R>
+__device__ __forceinline__ void bgk_pair_j(R& a, R& b, R w, R aw, R cj, R cF, R D, R inv_rho, R jj15, R uF3,
+                                           R omega, R om1, R beta) {
+    const R cu = cj * inv_rho;
+    const R E = w * D + w * ((R(4.5) * cj * cj - jj15) * inv_rho);
+    const R O = aw * cj;
+    const R bw = beta * w;
+    const R Se = bw * (R(9) * cu * cF - uF3);
+    const R So = (beta * aw) * cF;
+    a = om1 * a + (omega * (E + O) + (Se + So));
+    b = om1 * b + (omega * (E - O) + (Se - So));
+}
+
+// Equilibrium of one direction pair: v_i = w (D + rho (3 cu + 4.5 cu^2 - 1.5 u.u)).
+template <typename R>
+__device__ __forceinline__ void eq_pair(R& a, R& b, R w, R cu, R D, R rho, R uu15) {
+    const R E = w * D + (w * rho) * (R(4.5) * cu * cu - uu15);
+    const R O = R(3) * (w * rho) * cu;
+    a = E + O;
+    b = E - O;
+}
+
+// One node's collision, in place on v[19].
+template <typename R, bool SHIFT>
+__device__ __forceinline__ void collide(R v[Q], int type, const StepParams& p, R Fx, R Fy, R Fz) {
+    // moments from pair sums s and differences d of opposite directions
+    const R s13 = v[1] + v[3], s24 = v[2] + v[4], s56 = v[5] + v[6], s79 = v[7] + v[9], s810 = v[8] + v[10];
+    const R s1114 = v[11] + v[14], s1213 = v[12] + v[13], s1518 = v[15] + v[18], s1617 = v[16] + v[17];
+    const R d13 = v[1] - v[3], d24 = v[2] - v[4], d56 = v[5] - v[6], d79 = v[7] - v[9], d810 = v[8] - v[10];
+    const R d1114 = v[11] - v[14], d1213 = v[12] - v[13], d1518 = v[15] - v[18], d1617 = v[16] - v[17];
+    const R sum = ((v[0] + s13) + (s24 + s56)) + ((s79 + s810) + (s1114 + s1213)) + (s1518 + s1617);
+    const R jx = ((d13 + d79) - d810) + (d1114 + d1213);
+    const R jy = ((d24 + d79) + d810) + (d1518 + d1617);
+    const R jz = ((d56 + d1114) - d1213) + (d1518 - d1617);
+    R D, rho;
+    if (SHIFT) {
+        D = sum;
+        rho = R(1) + D;
+    } else {
+        rho = sum;
+        D = sum;
+    }
+    const R inv_rho = R(1) / rho;
+    const R Jx = jx + R(0.5) * Fx, Jy = jy + R(0.5) * Fy, Jz = jz + R(0.5) * Fz;
+    const R ux = Jx * inv_rho;
+    const R uy = Jy * inv_rho;
+    const R uz = Jz * inv_rho;
+    const R w0 = R(wgt(0)), w1 = R(wgt(1)), w2 = R(wgt(7));
+    if (SHIFT && type == LBM_FLUID) {
+        const R omega = par<R>(p.omega, p.omega_f), om1 = R(1) - omega, beta = par<R>(p.beta, p.beta_f);
+        const R jj15 = R(1.5) * (Jx * Jx + Jy * Jy + Jz * Jz);
+        const R uF3 = R(3) * (ux * Fx + uy * Fy + uz * Fz);
+        const R s0 = R(W0S), s1 = R(W1S), s2 = R(W2S), a1 = R(A1S), a2 = R(A2S);
+        v[0] = om1 * v[0] + (omega * (s0 * D - s0 * (jj15 * inv_rho)) - (beta * s0) * uF3);
+        bgk_pair_j(v[1], v[3], s1, a1, Jx, Fx, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[2], v[4], s1, a1, Jy, Fy, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[5], v[6], s1, a1, Jz, Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[7], v[9], s2, a2, Jx + Jy, Fx + Fy, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[8], v[10], s2, a2, Jy - Jx, Fy - Fx, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[11], v[14], s2, a2, Jx + Jz, Fx + Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[12], v[13], s2, a2, Jx - Jz, Fx - Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[15], v[18], s2, a2, Jy + Jz, Fy + Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+        bgk_pair_j(v[16], v[17], s2, a2, Jy - Jz, Fy - Fz, D, inv_rho, jj15, uF3, omega, om1, beta);
+    } else if (type == LBM_FLUID) {
+        const R omega = par<R>(p.omega, p.omega_f), om1 = R(1) - omega, beta = par<R>(p.beta, p.beta_f);
+        const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+        const R uF3 = R(3) * (ux * Fx + uy * Fy + uz * Fz);
+        v[0] = om1 * v[0] + (omega * (w0 * D - (w0 * rho) * uu15) - (beta * w0) * uF3);
+        bgk_pair(v[1], v[3], w1, ux, Fx, D, rho, uu15, uF3, omega, om1, beta);
+        bgk_pair(v[2], v[4], w1, uy, Fy, D, rho, uu15, uF3, omega, om1, beta);
+        bgk_pair(v[5], v[6], w1, uz, Fz, D, rho, uu15, uF3, omega, om1, beta);
+        bgk_pair(v[7], v[9], w2, ux + uy, Fx + Fy, D, rho, uu15, uF3, omega, om1, beta);
+        bgk_pair(v[8], v[10], w2, uy - ux, Fy - Fx, D, rho, uu15, uF3, omega, om1, beta);
+        bgk_pair(v[11], v[14], w2, ux + uz, Fx + Fz, D, rho, uu15, uF3, omega, om1, beta);
+        bgk_pair(v[12], v[13], w2, ux - uz, Fx - Fz, D, rho, uu15, uF3, omega, om1, beta);
+        bgk_pair(v[15], v[18], w2, uy + uz, Fy + Fz, D, rho, uu15, uF3, omega, om1, beta);
+        bgk_pair(v[16], v[17], w2, uy - uz, Fy - Fz, D, rho, uu15, uF3, omega, om1, beta);
+    } else {
+        // inlet: f^eq(rho, u_in); outlet: f^eq(rho_out, u)
+        R ex, ey, ez, Dq, rq;
+        if (type == LBM_INLET) {
+            ex = par<R>(p.u_in[0], p.u_in_f[0]);
+            ey = par<R>(p.u_in[1], p.u_in_f[1]);
+            ez = par<R>(p.u_in[2], p.u_in_f[2]);
+            Dq = D; rq = rho;
+        } else {
+            ex = ux; ey = uy; ez = uz;
+            rq = par<R>(p.rho_out, p.rho_out_f);
+            Dq = SHIFT ? par<R>(p.rho_out - 1.0, p.rho_out_m1_f) : rq;
+        }
+        const R uu15 = R(1.5) * (ex * ex + ey * ey + ez * ez);
+        v[0] = w0 * Dq - (w0 * rq) * uu15;
+        eq_pair(v[1], v[3], w1, ex, Dq, rq, uu15);
+        eq_pair(v[2], v[4], w1, ey, Dq, rq, uu15);
+        eq_pair(v[5], v[6], w1, ez, Dq, rq, uu15);
+        eq_pair(v[7], v[9], w2, ex + ey, Dq, rq, uu15);
+        eq_pair(v[8], v[10], w2, ey - ex, Dq, rq, uu15);
+        eq_pair(v[11], v[14], w2, ex + ez, Dq, rq, uu15);
+        eq_pair(v[12], v[13], w2, ex - ez, Dq, rq, uu15);
+        eq_pair(v[15], v[18], w2, ey + ez, Dq, rq, uu15);
+        eq_pair(v[16], v[17], w2, ey - ez, Dq, rq, uu15);
+    }
+}
+
+// ------------------------------------------------------------ stochastic rounding
+// MurmurHash3's 32-bit finaliser (A. Appleby, public domain): a bijective avalanche mix,
+// used as a counter-based generator keyed by (step counter, node, direction pair).
+__device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+    h ^= h >> 16;
+    h *= 0x85ebca6bu;
+    h ^= h >> 13;
+    h *= 0xc2b2ae35u;
+    h ^= h >> 16;
+    return h;
+}
+
+// binary16 nearest to x + d, d = (r - 32767.5) 2^-16 s uniform over one binary16 spacing
+// s of x (r: 16 random bits). For x in (lo, lo + s) this rounds up with probability
+// (x - lo) / s to 16 bits, i.e. stochastic rounding (the FP32 sum x + d is off by at most
+// 2^-14 s). s = 2^(e - 10) for |x| >= 2^-14 (e the exponent of x), 2^-24 below.
+__device__ __forceinline__ __half half_dithered(float x, uint32_t r) {
+    const uint32_t eb = __float_as_uint(x) & 0x7f800000u;
+    const uint32_t sb = max(eb, 113u << 23) - (26u << 23);   // s * 2^-16
+    const float d = __fmul_rn(__int2float_rn((int)r - 32767) - 0.5f, __uint_as_float(sb));
+    return __float2half_rn(__fadd_rn(x, d));
+}
+
+}  // namespace lbm

@@ -11,7 +11,8 @@
 //     omega f^eq_i = omega w (rho + 3 c.j' + Q_i),  Q_i = (4.5 (c.j')^2 - 1.5 |j'|^2) / rho,
 //     S_i = beta w (3 c.F - 3 u.F + 9 (c.u)(c.F)),
 // split per direction pair into the parts even in c,
-//     Ye = omega w (rho + Q) + 9 beta w (c.u)(c.F) - 3 beta w (u.F),
+//     Ye = omega w rho + (w / rho) (c.j' (4.5 omega c.j' + 9 beta c.F) - P),
+//     P  = 1.5 omega |j'|^2 + 3 beta j'.F   (once per node),
 // and odd in c, Yo = 3 omega w (c.j') + 3 beta w (c.F); Y_i = Ye + Yo, Y_inv(i) = Ye - Yo.
 #pragma once
 #include "lbm_df.cuh"
@@ -22,14 +23,16 @@ namespace lbm {
 // the rest weight 1/3, class 1 the axis weight 1/18, class 2 the diagonal weight 1/36.
 struct DFConst {
     double om1;          // 1 - omega
-    dfl ow[3];           // omega w
     double ow_d[3];      // omega w in FP64, for the dominant term omega w rho
     dfl ow3[3];          // 3 omega w
-    dfl bw[3];           // beta w
-    dfl bw3[3];          // 3 beta w
-    dfl bw9[3];          // 9 beta w
+    dfl om45, om15;      // 4.5 omega, 1.5 omega
+    dfl b3, b9;          // 3 beta, 9 beta
+    dfl w0, w1;          // 1/3, 1/18
+    dfl bw3;             // 3 beta w1
     dfl Fy, Fz;          // uniform y, z force density
-    double Fy_d, Fz_d;   // the same in FP64
+    dfl G9y, G9z;        // 9 beta F_y, 9 beta F_z
+    dfl G3y, G3z;        // 3 beta w1 F_y, 3 beta w1 F_z
+    double Fy_d, Fz_d;   // F_y, F_z in FP64
 };
 
 LBM_DF_HD dfl df_split_host(double v) {
@@ -42,27 +45,35 @@ LBM_DF_HD DFConst make_df_const(double omega, double beta, double Fy, double Fz)
     const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
     c.om1 = 1.0 - omega;
     for (int k = 0; k < 3; k++) {
-        c.ow[k] = df_split_host(omega * w[k]);
         c.ow_d[k] = omega * w[k];
         c.ow3[k] = df_split_host(3.0 * omega * w[k]);
-        c.bw[k] = df_split_host(beta * w[k]);
-        c.bw3[k] = df_split_host(3.0 * beta * w[k]);
-        c.bw9[k] = df_split_host(9.0 * beta * w[k]);
     }
+    c.om45 = df_split_host(4.5 * omega);
+    c.om15 = df_split_host(1.5 * omega);
+    c.b3 = df_split_host(3.0 * beta);
+    c.b9 = df_split_host(9.0 * beta);
+    c.w0 = df_split_host(w[0]);
+    c.w1 = df_split_host(w[1]);
+    c.bw3 = df_split_host(3.0 * beta * w[1]);
     c.Fy = df_split_host(Fy);
     c.Fz = df_split_host(Fz);
+    c.G9y = df_split_host(9.0 * beta * Fy);
+    c.G9z = df_split_host(9.0 * beta * Fz);
+    c.G3y = df_split_host(3.0 * beta * w[1] * Fy);
+    c.G3z = df_split_host(3.0 * beta * w[1] * Fz);
     c.Fy_d = Fy;
     c.Fz_d = Fz;
     return c;
 }
 
-// One direction pair (a with velocity c, b with -c) of weight class k.
-LBM_DF_HD void df_pair(double& a, double& b, const DFConst& K, int k, dfl cj, dfl cF, dfl inv, dfl A, dfl Gu,
-                       dfl JJ15) {
-    const dfl cu = df_mul(cj, inv);
-    const dfl Q = df_mul(df_sub(df_mulf(df_mul(cj, cj), 4.5f), JJ15), inv);
-    const dfl Ye = df_sub(df_add(df_add(A, df_mul(K.ow[k], Q)), df_mul(K.bw9[k], df_mul(cu, cF))), Gu);
-    const dfl Yo = df_add(df_mul(K.ow3[k], cj), df_mul(K.bw3[k], cF));
+// One direction pair (a with velocity c, b with -c) of weight class k, with
+//   cj = c.j', g9 = 9 beta c.F, g3 = 3 beta w c.F, winv = w / rho:
+//   Ye = A + winv (cj (4.5 omega cj + g9) - P),   Yo = 3 omega w cj + g3.
+LBM_DF_HD void df_pair(double& a, double& b, const DFConst& K, int k, dfl cj, dfl g9, dfl g3, dfl winv, dfl A,
+                       dfl P) {
+    const dfl T = df_sub(df_mul(cj, df_add(df_mul(K.om45, cj), g9)), P);
+    const dfl Ye = df_add(A, df_mul(winv, T));
+    const dfl Yo = df_add(df_mul(K.ow3[k], cj), g3);
     const double yp = df_to_double_pos(df_add(Ye, Yo));
     const double ym = df_to_double_pos(df_sub(Ye, Yo));
 #if defined(__CUDA_ARCH__)
@@ -93,14 +104,14 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K) {
     const dfl Jx = df_from_fix(jx + (fix_from_double(Fx) >> 1));
     const dfl Jy = df_from_fix(jy + (fix_from_double(K.Fy_d) >> 1));
     const dfl Jz = df_from_fix(jz + (fix_from_double(K.Fz_d) >> 1));
-    const dfl R = df_from_fix(rho);
-    const dfl inv = df_recip(R);
-    const dfl ux = df_mul(Jx, inv), uy = df_mul(Jy, inv), uz = df_mul(Jz, inv);
+    const dfl inv = df_recip(df_from_fix(rho));
     const dfl Fxd = df_from_double(Fx);
-    const dfl JJ15 = df_mulf(df_add(df_add(df_mul(Jx, Jx), df_mul(Jy, Jy)), df_mul(Jz, Jz)), 1.5f);
-    const dfl uF3 = df_mulf(df_add(df_add(df_mul(ux, Fxd), df_mul(uy, K.Fy)), df_mul(uz, K.Fz)), 3.0f);
-    dfl A[3], Gu[3];
-#pragma unroll
+    // P = 1.5 omega |j'|^2 + 3 beta j'.F: the isotropic second-order part of every Y_i
+    const dfl JJ = df_add(df_add(df_mul(Jx, Jx), df_mul(Jy, Jy)), df_mul(Jz, Jz));
+    const dfl JF = df_add(df_add(df_mul(Jx, Fxd), df_mul(Jy, K.Fy)), df_mul(Jz, K.Fz));
+    const dfl P = df_add(df_mul(K.om15, JJ), df_mul(K.b3, JF));
+    const dfl winv1 = df_mul(K.w1, inv);
+    const dfl winv2 = df_scale2(winv1, 0.5f);
     // omega w rho dominates every Y_i, so it is formed in FP64 (one conversion and three
     // multiplies per node): a double-float product with a rounded constant would leave a
     // systematic relative bias of ~1e-15 that acts as a mass source
@@ -109,26 +120,34 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K) {
 #else
     const double rho_d = (double)rho * (1.0 / (double)(1ull << FIX_SHIFT));
 #endif
-    for (int k = 0; k < 3; k++) {
-        A[k] = df_from_double(K.ow_d[k] * rho_d);
-        Gu[k] = df_mul(K.bw[k], uF3);
-    }
-    // rest population: Y0 = omega w0 (rho - 1.5 |j'|^2 / rho) - 3 beta w0 (u.F)
-    const dfl Y0 = df_sub(df_sub(A[0], df_mul(K.ow[0], df_mul(JJ15, inv))), Gu[0]);
+    dfl A[3];
+#pragma unroll
+    for (int k = 0; k < 3; k++) A[k] = df_from_double(K.ow_d[k] * rho_d);
+    // rest population: Y0 = A0 - (w0 / rho) P
+    const dfl Y0 = df_sub(A[0], df_mul(df_mul(K.w0, inv), P));
 #if defined(__CUDA_ARCH__)
     f[0] = __fma_rn(K.om1, f[0], df_to_double_pos(Y0));
 #else
     f[0] = std::fma(K.om1, f[0], df_to_double_pos(Y0));
 #endif
-    df_pair(f[1], f[3], K, 1, Jx, Fxd, inv, A[1], Gu[1], JJ15);
-    df_pair(f[2], f[4], K, 1, Jy, K.Fy, inv, A[1], Gu[1], JJ15);
-    df_pair(f[5], f[6], K, 1, Jz, K.Fz, inv, A[1], Gu[1], JJ15);
-    df_pair(f[7], f[9], K, 2, df_add(Jx, Jy), df_add(Fxd, K.Fy), inv, A[2], Gu[2], JJ15);
-    df_pair(f[8], f[10], K, 2, df_sub(Jy, Jx), df_sub(K.Fy, Fxd), inv, A[2], Gu[2], JJ15);
-    df_pair(f[11], f[14], K, 2, df_add(Jx, Jz), df_add(Fxd, K.Fz), inv, A[2], Gu[2], JJ15);
-    df_pair(f[12], f[13], K, 2, df_sub(Jx, Jz), df_sub(Fxd, K.Fz), inv, A[2], Gu[2], JJ15);
-    df_pair(f[15], f[18], K, 2, df_add(Jy, Jz), df_add(K.Fy, K.Fz), inv, A[2], Gu[2], JJ15);
-    df_pair(f[16], f[17], K, 2, df_sub(Jy, Jz), df_sub(K.Fy, K.Fz), inv, A[2], Gu[2], JJ15);
+    // force terms per axis; a diagonal pair's are sums, and its 3 beta w c.F is half the
+    // axis value (w2 = w1 / 2)
+    const dfl G9x = df_mul(K.b9, Fxd), G3x = df_mul(K.bw3, Fxd);
+    df_pair(f[1], f[3], K, 1, Jx, G9x, G3x, winv1, A[1], P);
+    df_pair(f[2], f[4], K, 1, Jy, K.G9y, K.G3y, winv1, A[1], P);
+    df_pair(f[5], f[6], K, 1, Jz, K.G9z, K.G3z, winv1, A[1], P);
+    df_pair(f[7], f[9], K, 2, df_add(Jx, Jy), df_add(G9x, K.G9y), df_scale2(df_add(G3x, K.G3y), 0.5f), winv2, A[2],
+            P);
+    df_pair(f[8], f[10], K, 2, df_sub(Jy, Jx), df_sub(K.G9y, G9x), df_scale2(df_sub(K.G3y, G3x), 0.5f), winv2,
+            A[2], P);
+    df_pair(f[11], f[14], K, 2, df_add(Jx, Jz), df_add(G9x, K.G9z), df_scale2(df_add(G3x, K.G3z), 0.5f), winv2,
+            A[2], P);
+    df_pair(f[12], f[13], K, 2, df_sub(Jx, Jz), df_sub(G9x, K.G9z), df_scale2(df_sub(G3x, K.G3z), 0.5f), winv2,
+            A[2], P);
+    df_pair(f[15], f[18], K, 2, df_add(Jy, Jz), df_add(K.G9y, K.G9z), df_scale2(df_add(K.G3y, K.G3z), 0.5f), winv2,
+            A[2], P);
+    df_pair(f[16], f[17], K, 2, df_sub(Jy, Jz), df_sub(K.G9y, K.G9z), df_scale2(df_sub(K.G3y, K.G3z), 0.5f), winv2,
+            A[2], P);
 }
 
 }  // namespace lbm
