@@ -130,6 +130,136 @@ void oracle_collide(const double f[Q], int type, double tau, const double F[3],
 }
 
 /* ---------------------------------------------------------------------------- */
+/* Collision models beyond quasi-compressible LBGK (the paper's other variants).
+ *
+ * eq = 0: quasi-compressible equilibrium, Eq. 3 with u from Eq. 5 (the default above).
+ * eq = 1: incompressible equilibrium, Eq. 4 with u from Eq. 6: f^eq_i = w_i (rho +
+ *         3 c.u + 4.5 (c.u)^2 - 1.5 u.u), u = sum c f (+ F/2 with Guo forcing, the
+ *         reference density rho_0 = 1 taking the place of rho in u).
+ * coll = 0: LBGK, Eq. 2 / Eq. 7.
+ * coll = 1: multiple relaxation times, Eq. 8, in the D3Q19 moment basis of d'Humieres,
+ *         Ginzburg, Krafczyk, Lallemand and Luo (Phil. Trans. R. Soc. A 360, 2002):
+ *         m = M f, m* = m - S (m - m^eq) + (I - S/2) M G, f* = M^-1 m*, with
+ *         m^eq = M f^eq (the projection of the equilibrium above, so that S = I/tau is
+ *         LBGK exactly) and G_i = w_i [3 (c_i - u).F + 9 (c_i.u)(c_i.F)] the Guo force
+ *         term without its (1 - 1/(2 tau)) factor (Guo et al. 2002, in moment space).
+ * rates: the 19 diagonal entries of S in moment order (below).
+ *
+ * Moment basis: each row is a polynomial in the velocity c (|c|^2 = c.c), evaluated
+ * on the 19 velocities, in this order:
+ *   0 rho = 1,                  1 e = 19 |c|^2 - 30,
+ *   2 eps = (21 |c|^4 - 53 |c|^2 + 24) / 2,
+ *   3 j_x = c_x,  4 q_x = (5 |c|^2 - 9) c_x,  5 j_y,  6 q_y,  7 j_z,  8 q_z,
+ *   9 3p_xx = 3 c_x^2 - |c|^2,  10 3pi_xx = (3 |c|^2 - 5)(3 c_x^2 - |c|^2),
+ *  11 p_ww = c_y^2 - c_z^2,     12 pi_ww = (3 |c|^2 - 5)(c_y^2 - c_z^2),
+ *  13 p_xy = c_x c_y,  14 p_yz = c_y c_z,  15 p_xz = c_x c_z,
+ *  16 m_x = (c_y^2 - c_z^2) c_x,  17 m_y = (c_z^2 - c_x^2) c_y,  18 m_z = (c_x^2 - c_y^2) c_z.
+ * The rows are mutually orthogonal, so M^-1 = M^T diag(1 / |row|^2). */
+static double basis(int k, const int c[3]) {
+    const double x = c[0], y = c[1], z = c[2], cc = x * x + y * y + z * z;
+    switch (k) {
+        case 0: return 1.0;
+        case 1: return 19.0 * cc - 30.0;
+        case 2: return (21.0 * cc * cc - 53.0 * cc + 24.0) / 2.0;
+        case 3: return x;
+        case 4: return (5.0 * cc - 9.0) * x;
+        case 5: return y;
+        case 6: return (5.0 * cc - 9.0) * y;
+        case 7: return z;
+        case 8: return (5.0 * cc - 9.0) * z;
+        case 9: return 3.0 * x * x - cc;
+        case 10: return (3.0 * cc - 5.0) * (3.0 * x * x - cc);
+        case 11: return y * y - z * z;
+        case 12: return (3.0 * cc - 5.0) * (y * y - z * z);
+        case 13: return x * y;
+        case 14: return y * z;
+        case 15: return x * z;
+        case 16: return (y * y - z * z) * x;
+        case 17: return (z * z - x * x) * y;
+        default: return (x * x - y * y) * z;
+    }
+}
+
+/* The moment matrix M[k][i] (row-major), exported for the tests. */
+void oracle_mrt_matrix(double* M) {
+    for (int k = 0; k < Q; k++)
+        for (int i = 0; i < Q; i++) M[k * Q + i] = basis(k, C[i]);
+}
+
+/* Equilibrium of either model (eq = 0 Eq. 3, eq = 1 Eq. 4). */
+static double feq_m(int i, int eq, double rho, const double u[3]) {
+    if (eq == 0) return feq(i, rho, u);
+    double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+    double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    return W[i] * (rho + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+}
+
+/* Velocity used in the collision: Eq. 5 (eq = 0) or Eq. 6 (eq = 1), with F/2. */
+static void velocity_m(int eq, double rho, const double j[3], const double F[3], double u[3]) {
+    for (int a = 0; a < 3; a++) u[a] = eq == 0 ? (j[a] + 0.5 * F[a]) / rho : j[a] + 0.5 * F[a];
+}
+
+void oracle_collide_m(const double f[Q], int type, double tau, const double F[3], const double u_in[3],
+                      double rho_out, int eq, int coll, const double rates[Q], double out[Q]) {
+    if (eq == 0 && coll == 0) {
+        oracle_collide(f, type, tau, F, u_in, rho_out, out);
+        return;
+    }
+    double rho, j[3], u[3];
+    moments(f, &rho, j);
+    velocity_m(eq, rho, j, F, u);
+    if (type == INLET) {
+        for (int i = 0; i < Q; i++) out[i] = feq_m(i, eq, rho, u_in);
+        return;
+    }
+    if (type == OUTLET) {
+        for (int i = 0; i < Q; i++) out[i] = feq_m(i, eq, rho_out, u);
+        return;
+    }
+    double fe[Q], G[Q];
+    for (int i = 0; i < Q; i++) {
+        double cu = C[i][0] * u[0] + C[i][1] * u[1] + C[i][2] * u[2];
+        double cF = C[i][0] * F[0] + C[i][1] * F[1] + C[i][2] * F[2];
+        double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+        fe[i] = feq_m(i, eq, rho, u);
+        G[i] = W[i] * (3.0 * (cF - uF) + 9.0 * cu * cF);
+    }
+    if (coll == 0) {
+        for (int i = 0; i < Q; i++) out[i] = f[i] - (f[i] - fe[i]) / tau + (1.0 - 0.5 / tau) * G[i];
+        return;
+    }
+    /* MRT: relax in moment space, then back with M^-1 = M^T diag(1/|row|^2) */
+    double M[Q][Q], mstar[Q];
+    for (int k = 0; k < Q; k++)
+        for (int i = 0; i < Q; i++) M[k][i] = basis(k, C[i]);
+    for (int k = 0; k < Q; k++) {
+        double m = 0.0, meq = 0.0, mG = 0.0, norm = 0.0;
+        for (int i = 0; i < Q; i++) {
+            m += M[k][i] * f[i];
+            meq += M[k][i] * fe[i];
+            mG += M[k][i] * G[i];
+            norm += M[k][i] * M[k][i];
+        }
+        mstar[k] = (m - rates[k] * (m - meq) + (1.0 - 0.5 * rates[k]) * mG) / norm;
+    }
+    for (int i = 0; i < Q; i++) {
+        double v = 0.0;
+        for (int k = 0; k < Q; k++) v += M[k][i] * mstar[k];
+        out[i] = v;
+    }
+}
+
+/* oracle_step with a collision model (eq, coll, rates as for oracle_collide_m). */
+void oracle_step_m(const double* A, double* B, const uint8_t* nt, int nx, int ny, int nz, unsigned periodic,
+                   double tau, const double g[3], const double* g_field, const double u_in[3], double rho_out,
+                   int eq, int coll, const double rates[Q], int nthreads);
+
+/* Macroscopic fields of either model: u = (sum c f* - F/2) / rho (eq = 0, reading R6) or
+ * u = sum c f* - F/2 (eq = 1, Eq. 6). */
+void oracle_macroscopic_m(const double* f, const uint8_t* nt, long N, const double g[3], const double* g_field,
+                          int eq, double* rho, double* u);
+
+/* ---------------------------------------------------------------------------- */
 /* Streaming source of direction i at node (x,y,z): the node x - c_i, wrapped on
  * periodic axes (bit 0: x, bit 1: y, bit 2: z). Returns 0 when it leaves the box. */
 static int source_node(int x, int y, int z, int i, int nx, int ny, int nz,
@@ -180,6 +310,31 @@ void oracle_step(const double* A, double* B, const uint8_t* nt, int nx, int ny, 
             }
 }
 
+void oracle_step_m(const double* A, double* B, const uint8_t* nt, int nx, int ny, int nz, unsigned periodic,
+                   double tau, const double g[3], const double* g_field, const double u_in[3], double rho_out,
+                   int eq, int coll, const double rates[Q], int nthreads) {
+    long N = (long)nx * ny * nz;
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+    for (int z = 0; z < nz; z++)
+        for (int y = 0; y < ny; y++)
+            for (int x = 0; x < nx; x++) {
+                long n = x + (long)nx * (y + (long)ny * z);
+                if (nt[n] == SOLID) continue;
+                double f[Q], out[Q], F[3];
+                for (int i = 0; i < Q; i++) {
+                    long s;
+                    if (source_node(x, y, z, i, nx, ny, nz, periodic, &s) && nt[s] != SOLID)
+                        f[i] = A[i * N + s];
+                    else
+                        f[i] = A[opp(i) * N + n];
+                }
+                force_at(n, g, g_field, F);
+                oracle_collide_m(f, nt[n], tau, F, u_in, rho_out, eq, coll, rates, out);
+                for (int i = 0; i < Q; i++) B[i * N + n] = out[i];
+            }
+}
+
 /* Equilibrium initial state f = f^eq(rho0, u0) at non-solid nodes, NaN at solid. */
 void oracle_init(double* f, const uint8_t* nt, long N, double rho0, const double u0[3]) {
     for (long n = 0; n < N; n++)
@@ -202,6 +357,27 @@ void oracle_macroscopic(const double* f, const uint8_t* nt, long N, const double
         force_at(n, g, g_field, F);
         rho[n] = r;
         for (int a = 0; a < 3; a++) u[a * N + n] = (j[a] - 0.5 * F[a]) / r;
+    }
+}
+
+void oracle_macroscopic_m(const double* f, const uint8_t* nt, long N, const double g[3], const double* g_field,
+                          int eq, double* rho, double* u) {
+    if (eq == 0) {
+        oracle_macroscopic(f, nt, N, g, g_field, rho, u);
+        return;
+    }
+    for (long n = 0; n < N; n++) {
+        if (nt[n] == SOLID) {
+            rho[n] = 0.0;
+            u[n] = u[N + n] = u[2 * N + n] = 0.0;
+            continue;
+        }
+        double fl[Q], r, j[3], F[3];
+        for (int i = 0; i < Q; i++) fl[i] = f[i * N + n];
+        moments(fl, &r, j);
+        force_at(n, g, g_field, F);
+        rho[n] = r;
+        for (int a = 0; a < 3; a++) u[a * N + n] = j[a] - 0.5 * F[a];
     }
 }
 

@@ -43,6 +43,10 @@ def load(path):
     L.oracle_step_tl.argtypes = [d, d, d, d, u8, ci, ci, ci, cu, cd, cd, d, d, d, d, d, cd]
     L.oracle_collide_adj.argtypes = [d, ci, cd, d, d, cd, d, d, d, d]
     L.oracle_step_adj.argtypes = [d, d, d, u8, ci, ci, ci, cu, cd, d, d, d, cd, d, d, d]
+    L.oracle_mrt_matrix.argtypes = [d]
+    L.oracle_collide_m.argtypes = [d, ci, cd, d, d, cd, ci, ci, d, d]
+    L.oracle_step_m.argtypes = [d, d, u8, ci, ci, ci, cu, cd, d, d, d, cd, ci, ci, d, ci]
+    L.oracle_macroscopic_m.argtypes = [d, u8, cl, d, d, ci, d, d]
     L.oracle_loss.argtypes = [d, u8, ci, ci, ci, ci, d, d, d, d, d]
     L.oracle_loss.restype = cd
     return L
@@ -271,3 +275,76 @@ def nonsolid(nt):
 
 def default_threads():
     return os.cpu_count() or 1
+
+
+# ------------------------------------------------------------------ collision models
+EQ_QCOMPR, EQ_INCOMPR = 0, 1
+COLL_BGK, COLL_MRT = 0, 1
+
+
+def mrt_matrix():
+    """The D3Q19 moment matrix M[k, i] (d'Humieres et al. 2002 basis)."""
+    M = np.zeros((Q, Q))
+    lib().oracle_mrt_matrix(_p(M))
+    return M
+
+
+def mrt_rates(tau, s_e=1.19, s_eps=1.4, s_q=1.2, s_pi=1.4, s_m=1.98):
+    """The 19 relaxation rates in moment order; the viscous moments relax with 1/tau.
+    Defaults: the rates d'Humieres et al. (2002) suggest for D3Q19; the conserved
+    moments' rates are 1 (they do not enter the update)."""
+    s_nu = 1.0 / tau
+    return np.array([1.0, s_e, s_eps, 1.0, s_q, 1.0, s_q, 1.0, s_q, s_nu, s_pi, s_nu, s_pi,
+                     s_nu, s_nu, s_nu, s_m, s_m, s_m])
+
+
+def _rates(rates):
+    if rates is None:
+        return np.zeros(Q)
+    r = _f64(rates).reshape(Q)
+    return r
+
+
+def collide_m(f, node_type, tau, F=(0, 0, 0), u_in=(0, 0, 0), rho_out=1.0, eq=EQ_QCOMPR, coll=COLL_BGK,
+              rates=None):
+    f = _f64(f).reshape(Q)
+    out = np.zeros(Q)
+    r = _rates(rates)
+    lib().oracle_collide_m(_p(f), int(node_type), float(tau), _p(_d3(F)), _p(_d3(u_in)), float(rho_out),
+                           int(eq), int(coll), _p(r), _p(out))
+    return out
+
+
+def step_m(A, nt, periodic, tau, g=(0, 0, 0), g_field=None, u_in=(0, 0, 0), rho_out=1.0, eq=EQ_QCOMPR,
+           coll=COLL_BGK, rates=None, nthreads=1, out=None):
+    nt = _u8(nt)
+    A = _f64(A)
+    nz, ny, nx = nt.shape
+    B = A.copy() if out is None else out
+    gf = None if g_field is None else _f64(g_field)
+    r = _rates(rates)
+    lib().oracle_step_m(_p(A), _p(B), _p(nt, ct.c_uint8), nx, ny, nz, int(periodic), float(tau), _p(_d3(g)),
+                        _p(gf), _p(_d3(u_in)), float(rho_out), int(eq), int(coll), _p(r), int(nthreads))
+    return B
+
+
+def run_m(f, nt, steps, periodic, tau, g=(0, 0, 0), g_field=None, u_in=(0, 0, 0), rho_out=1.0, eq=EQ_QCOMPR,
+          coll=COLL_BGK, rates=None, nthreads=1):
+    """``steps`` fused steps of the chosen collision model; returns the final state."""
+    A = _f64(f).copy()
+    B = A.copy()
+    for _ in range(steps):
+        step_m(A, nt, periodic, tau, g, g_field, u_in, rho_out, eq, coll, rates, nthreads, out=B)
+        A, B = B, A
+    return A
+
+
+def macroscopic_m(f, nt, g=(0, 0, 0), g_field=None, eq=EQ_QCOMPR):
+    nt = _u8(nt)
+    nz, ny, nx = nt.shape
+    N = nx * ny * nz
+    rho = np.zeros((nz, ny, nx))
+    u = np.zeros((3, nz, ny, nx))
+    gf = None if g_field is None else _f64(g_field)
+    lib().oracle_macroscopic_m(_p(_f64(f)), _p(nt, ct.c_uint8), N, _p(_d3(g)), _p(gf), int(eq), _p(rho), _p(u))
+    return rho, u

@@ -16,8 +16,9 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "oracle.c")
 
 MUTANTS = [
-    ("feq quadratic coefficient", "+ 4.5 * cu * cu - 1.5 * uu);\n}", "+ 4.0 * cu * cu - 1.5 * uu);\n}"),
-    ("feq u^2 sign", "4.5 * cu * cu - 1.5 * uu);\n}", "4.5 * cu * cu + 1.5 * uu);\n}"),
+    ("feq quadratic coefficient", "rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);\n}",
+     "rho * (1.0 + 3.0 * cu + 4.0 * cu * cu - 1.5 * uu);\n}"),
+    ("feq u^2 sign", "rho * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);\n}", "rho * (1.0 + 3.0 * cu + 4.5 * cu * cu + 1.5 * uu);\n}"),
     ("feq linear coefficient", "(1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);\n}", "(1.0 + 2.0 * cu + 4.5 * cu * cu - 1.5 * uu);\n}"),
     ("Guo prefactor", "return (1.0 - 0.5 / tau) * W[i]", "return (1.0 - 1.0 / tau) * W[i]"),
     ("Guo u.F sign", "3.0 * (cF - uF) + 9.0 * cu * cF);\n}", "3.0 * (cF + uF) + 9.0 * cu * cF);\n}"),
@@ -28,12 +29,17 @@ MUTANTS = [
     ("inlet density", "out[i] = feq(i, rho, u_in);", "out[i] = feq(i, 1.0, u_in);"),
     ("outlet density", "out[i] = feq(i, rho_out, u);", "out[i] = feq(i, rho, u);"),
     ("bounce-back takes own direction",
-     "f[i] = A[opp(i) * N + n];\n                }\n                force_at", "f[i] = A[i * N + n];\n                }\n                force_at"),
+     "f[i] = A[opp(i) * N + n];\n                }\n                force_at(n, g, g_field, F);\n                oracle_collide(f,",
+     "f[i] = A[i * N + n];\n                }\n                force_at(n, g, g_field, F);\n                oracle_collide(f,"),
     ("push instead of pull", "int p[3] = {x - C[i][0], y - C[i][1], z - C[i][2]};", "int p[3] = {x + C[i][0], y + C[i][1], z + C[i][2]};"),
     ("periodic wrap off by one", "p[a] = (p[a] + n[a]) % n[a];", "p[a] = (p[a] + n[a] + 1) % n[a];"),
     ("gather from solid nodes",
-     "if (source_node(x, y, z, i, nx, ny, nz, periodic, &s) && nt[s] != SOLID)\n                        f[i] = A[i * N + s];",
-     "if (source_node(x, y, z, i, nx, ny, nz, periodic, &s))\n                        f[i] = A[i * N + s];"),
+     "if (source_node(x, y, z, i, nx, ny, nz, periodic, &s) && nt[s] != SOLID)\n                        f[i] = A[i * N + s];\n"
+     "                    else\n                        f[i] = A[opp(i) * N + n];\n                }\n                force_at(n, g, g_field, F);\n"
+     "                oracle_collide(f,",
+     "if (source_node(x, y, z, i, nx, ny, nz, periodic, &s))\n                        f[i] = A[i * N + s];\n"
+     "                    else\n                        f[i] = A[opp(i) * N + n];\n                }\n                force_at(n, g, g_field, F);\n"
+     "                oracle_collide(f,"),
     ("diagonal weight", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0};", "1.0 / 36.0, 1.0 / 36.0, 1.0 / 36.0, 1.0 / 35.0};"),
     ("velocity table", "{0, -1, 1}, {0, -1, -1}};", "{0, -1, 1}, {0, 1, -1}};"),
     ("reported velocity shift sign", "u[a * N + n] = (j[a] - 0.5 * F[a]) / r;", "u[a * N + n] = (j[a] + 0.5 * F[a]) / r;"),
@@ -49,12 +55,26 @@ MUTANTS = [
     ("adjoint: Guo prefactor derivative", "lam[i] * W[i] * qi * 0.5 / (tau * tau);", "lam[i] * W[i] * qi * 0.5 / tau;"),
     ("loss seed sign", "lam[i * N + n] = (C[i][0] - ux) / r / (double)count;", "lam[i * N + n] = (C[i][0] + ux) / r / (double)count;"),
     ("tangent quotient rule", "(a.d * b.v - a.v * b.d) / (b.v * b.v)", "(a.d * b.v + a.v * b.d) / (b.v * b.v)"),
+    ("MRT energy row", "case 1: return 19.0 * cc - 30.0;", "case 1: return 19.0 * cc - 29.0;"),
+    ("MRT q row", "case 4: return (5.0 * cc - 9.0) * x;", "case 4: return (5.0 * cc - 8.0) * x;"),
+    ("MRT m_y row component", "case 17: return (z * z - x * x) * y;", "case 17: return (z * z - x * x) * x;"),
+    ("MRT force factor", "(1.0 - 0.5 * rates[k]) * mG", "(1.0 - rates[k]) * mG"),
+    ("MRT relaxes towards m", "mstar[k] = (m - rates[k] * (m - meq)", "mstar[k] = (m - rates[k] * (meq - m)"),
+    ("MRT inverse without norm", ") * mG) / norm;", ") * mG) / 1.0;"),
+    ("incompressible feq linear term", "return W[i] * (rho + 3.0 * cu", "return W[i] * (rho + 3.0 * rho * cu"),
+    ("incompressible velocity divides by rho", "? (j[a] + 0.5 * F[a]) / rho : j[a] + 0.5 * F[a];",
+     "? (j[a] + 0.5 * F[a]) / rho : (j[a] + 0.5 * F[a]) / rho;"),
+    ("incompressible reported velocity", "u[a * N + n] = j[a] - 0.5 * F[a];", "u[a * N + n] = j[a] + 0.5 * F[a];"),
+    ("model step bounce-back", "f[i] = A[opp(i) * N + n];\n                }\n                force_at(n, g, g_field, F);\n"
+     "                oracle_collide_m(", "f[i] = A[i * N + n];\n                }\n                force_at(n, g, g_field, F);\n"
+     "                oracle_collide_m("),
 ]
 
 
 def _battery():
     """Pins in order of cost; returns the name of the first that fails, or None."""
     import test_oracle_adjoint as A
+    import test_oracle_models as Mo
     import test_oracle_pins as P
     checks = [
         ("lattice constants", P.test_lattice_matches_paper_constants),
@@ -77,6 +97,14 @@ def _battery():
         ("loss gradient", lambda: A.test_loss_gradient_matches_fd(True)),
         ("shear wave", P.test_shear_wave_decay_rate),
         ("Poiseuille", P.test_poiseuille_closed_form),
+        ("MRT basis", Mo.test_basis_orthogonal_with_published_norms),
+        ("equilibrium moments", lambda: [Mo.test_equilibrium_moments_match_published_closed_forms(e) for e in (0, 1)]),
+        ("MRT = LBGK", lambda: [Mo.test_mrt_with_equal_rates_is_lbgk(e) for e in (0, 1)]),
+        ("incompressible LBGK", Mo.test_lbgk_incompressible_from_collide_m_matches_definition),
+        ("single moment", lambda: [Mo.test_single_moment_relaxes_by_its_own_rate(k) for k in (1, 2, 4, 9, 10, 16)]),
+        ("MRT conservation", lambda: [Mo.test_mrt_conserves_mass_and_adds_force(e) for e in (0, 1)]),
+        ("incompressible momentum", lambda: [Mo.test_incompressible_momentum_closed_form(c) for c in (0, 1)]),
+        ("magic Poiseuille", lambda: [Mo.test_poiseuille_exact_at_magic_lambda(e, c) for e in (0, 1) for c in (0, 1)]),
     ]
     for name, fn in checks:
         try:
