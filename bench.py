@@ -367,6 +367,9 @@ def main():
                     help="the fused step, or one of the paper's calibration kernels (propagation "
                          "only, read/write only)")
     ap.add_argument("--adjoint", action="store_true", help="run the adjoint workload instead")
+    ap.add_argument("--model", default="bgk", choices=list(MODELS),
+                    help="collision model: LBGK (Eq. 3, the benchmark), incompressible LBGK (Eq. 4), "
+                         "MRT (Eq. 8) with either equilibrium")
     ap.add_argument("--workload", default="porous", choices=["porous", "poiseuille", "vessel", "precision"],
                     help="porous is the benchmark line; the others print their own JSON line")
     ap.add_argument("--adj-steps", type=int, default=2000)
@@ -412,6 +415,9 @@ def main():
     L = lbm.Lattice(nt, args.dtype, 0b111, stream)
     info = L.info()
     L.set_params(tau, g)
+    eq_m, coll_m = MODELS[args.model]
+    if args.model != "bgk":
+        L.set_model(eq_m, coll_m)
     L.init_equilibrium()
     n_nonsolid = info["n_nonsolid"]
     kind = {"full": lbm.KERNEL_FULL, "propagate": lbm.KERNEL_PROPAGATE, "rw": lbm.KERNEL_RW}[args.kernel]
@@ -470,7 +476,7 @@ def main():
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (probe measured 1.20)",
                 "fp64_flops_per_node_update": flops_per_node,
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak}}
-    roof["traffic"] = TRAFFIC_PER_NODE.get(args.dtype) if args.kernel == "full" else None
+    roof["traffic"] = TRAFFIC_PER_NODE.get(args.dtype) if args.kernel == "full" and args.model == "bgk" else None
     if roof["traffic"] is not None and args.size == 256:
         roof["traffic"] = roof["traffic"] * n_nonsolid
         roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 128^3 "
@@ -486,6 +492,7 @@ def main():
                                   "propagate": "calibration: propagation only (gather with bounce-back, store)",
                                   "rw": "calibration: read/write only (own values, no propagation)"}[args.kernel],
                        "storage": DTYPE_NAME[args.dtype], "n_nonsolid": n_nonsolid,
+                       "collision_model": MODEL_NAME[args.model],
                        "n_tiles": info["n_tiles"], "eta_t": info["eta_t"],
                        "state_bytes": 2 * info["copy_bytes"],
                        "l2_policy": "inputs larger than L2 (two population copies of "
@@ -504,6 +511,8 @@ def main():
         t0 = time.perf_counter()
         ctx = lbm.lbm_create(pinned_nt.numpy(), nx, ny, nz, 4, lbm.DTYPES[args.dtype], 0b111, stream)
         lbm.lbm_set_params(ctx, tau, g)
+        if args.model != "bgk":
+            lbm.lbm_set_model(ctx, eq_m, coll_m)
         lbm.lbm_init_equilibrium(ctx)
         lbm.lbm_step(ctx, args.steps)
         mass_e2e, _ = lbm.lbm_reduce(ctx)
@@ -530,6 +539,13 @@ def main():
     if world > 1:
         dist.destroy_process_group()
 
+
+# Collision models: (equilibrium, collision) of lbm_set_model.
+MODELS = {"bgk": (0, 0), "bgk-incompr": (1, 0), "mrt": (0, 1), "mrt-incompr": (1, 1)}
+MODEL_NAME = {"bgk": "LBGK, quasi-compressible equilibrium (Eq. 3)",
+              "bgk-incompr": "LBGK, incompressible equilibrium (Eq. 4, 6)",
+              "mrt": "MRT (Eq. 8, d'Humieres et al. 2002 rates), quasi-compressible equilibrium",
+              "mrt-incompr": "MRT (Eq. 8, d'Humieres et al. 2002 rates), incompressible equilibrium"}
 
 # Executed FP64 FLOPs per non-solid node update of the all-FP64 step kernel: ncu counts
 # of 2 * dfma + dadd + dmul over one launch on the 128^3 pack, divided by its 732 512 nodes.

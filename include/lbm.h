@@ -118,8 +118,24 @@ lbm_status lbm_set_stream(lbm_ctx* ctx, void* stream);
 lbm_status lbm_set_params(lbm_ctx* ctx, double tau, const double* g, const double* g_field,
                           int g_field_on_device, const double* u_in, double rho_out);
 
-/* Set both population copies to the equilibrium f^eq(rho0, u0) of Eq. 3 at every
- * non-solid node. */
+/* Collision model: the paper's variants (Sec. 2.2). equilibrium: LBM_EQ_QCOMPR (Eq. 3,
+ * velocity Eq. 5; the default) or LBM_EQ_INCOMPR (Eq. 4, velocity Eq. 6: u = sum c f + F/2,
+ * the reference density 1 in place of rho). collision: LBM_COLL_BGK (Eq. 2 / Eq. 7; the
+ * default) or LBM_COLL_MRT (Eq. 8) in the D3Q19 moment basis of d'Humieres et al. (Phil.
+ * Trans. R. Soc. A 360, 2002), equilibrium moments the projection of the equilibrium above
+ * (so equal rates give LBGK), Guo forcing applied in moment space. rates: NULL for
+ * d'Humieres et al.'s suggested D3Q19 rates, else 5 host doubles {s_e, s_eps, s_q, s_pi,
+ * s_m} in (0, 2); the stress moments relax with 1/tau, the conserved ones with 1.
+ * Applies to lbm_step, lbm_init_equilibrium and lbm_macroscopic (u = sum c f* - F/2 for
+ * LBM_EQ_INCOMPR). Other models run their arithmetic in FP64 for the FP64 storage formats
+ * and in FP32 on h = f - w for the others. LBM_EINVAL for an unknown model or a rate outside
+ * (0, 2); lbm_adjoint supports only the default model. */
+enum { LBM_EQ_QCOMPR = 0, LBM_EQ_INCOMPR = 1 };
+enum { LBM_COLL_BGK = 0, LBM_COLL_MRT = 1 };
+lbm_status lbm_set_model(lbm_ctx* ctx, int equilibrium, int collision, const double* rates);
+
+/* Set both population copies to the equilibrium f^eq(rho0, u0) of the context's model
+ * (Eq. 3 by default) at every non-solid node. */
 lbm_status lbm_init_equilibrium(lbm_ctx* ctx, double rho0, const double* u0);
 
 /* Advance n >= 0 time steps: n launches of the fused step kernel, each reading the
@@ -137,7 +153,7 @@ lbm_status lbm_step_kernel(lbm_ctx* ctx, int kind, int n);
 
 /* Density and velocity from the stored post-collision populations f*:
  * rho = sum_i f*_i, u = (sum_i c_i f*_i - F/2) / rho (Eq. 5 with the half-force shift of
- * Guo forcing); 0 at solid nodes. rho: nx*ny*nz values, u: 3*nx*ny*nz values, dense,
+ * Guo forcing; Eq. 6, without the division, for LBM_EQ_INCOMPR); 0 at solid nodes. rho: nx*ny*nz values, u: 3*nx*ny*nz values, dense,
  * double if out_f64 else float; device pointers if on_device, else host. */
 lbm_status lbm_macroscopic(lbm_ctx* ctx, void* rho, void* u, int out_f64, int on_device);
 

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "lbm_collide.cuh"
 #include "lbm_internal.cuh"
 
 namespace lbm {
@@ -163,6 +164,22 @@ lbm_status geometry_hash(lbm_ctx* c, uint64_t* out) {
     int32_t dims[4] = {c->nx, c->ny, c->nz, (int32_t)c->periodic};
     *out = fnv1a(nt.data(), nt.size(), fnv1a(dims, sizeof(dims)));
     return LBM_OK;
+}
+
+// MRT relaxation constants of the step: rates in moment order (conserved moments 1,
+// stress moments 1/tau, the others from the user's five), divided by the row norms.
+void set_mrt_constants(lbm_ctx* c) {
+    const double* r = c->mrt_user;   // s_e, s_eps, s_q, s_pi, s_m
+    const double snu = c->tau > 0.5 ? 1.0 / c->tau : 1.0;
+    const double s[lbm::Q] = {1.0, r[0], r[1], 1.0, r[2], 1.0, r[2], 1.0, r[2], snu,
+                              r[3], snu, r[3], snu, snu, snu, r[4], r[4], r[4]};
+    for (int k = 0; k < lbm::Q; k++) {
+        const double n = (double)lbm::mrt_norm(k);
+        c->p.mrt_a[k] = (1.0 - s[k]) / n;
+        c->p.mrt_b[k] = (1.0 - 0.5 * s[k]) / n;
+        c->p.mrt_a_f[k] = (float)c->p.mrt_a[k];
+        c->p.mrt_b_f[k] = (float)c->p.mrt_b[k];
+    }
 }
 
 }  // namespace
@@ -423,7 +440,27 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
     }
     c->p.rho_out_f = (float)rho_out;
     c->p.rho_out_m1_f = (float)(rho_out - 1.0);
+    set_mrt_constants(c);
     c->params_set = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_set_model(lbm_ctx* c, int equilibrium, int collision, const double* rates) {
+    LBM_CHECK_CTX(c);
+    if (equilibrium != LBM_EQ_QCOMPR && equilibrium != LBM_EQ_INCOMPR)
+        return fail(c, LBM_EINVAL, "unknown equilibrium");
+    if (collision != LBM_COLL_BGK && collision != LBM_COLL_MRT) return fail(c, LBM_EINVAL, "unknown collision");
+    if (rates)
+        for (int k = 0; k < 5; k++)
+            if (!(std::isfinite(rates[k]) && rates[k] > 0.0 && rates[k] < 2.0))
+                return fail(c, LBM_EINVAL, "MRT rates must lie in (0, 2)");
+    const double defaults[5] = {1.19, 1.4, 1.2, 1.4, 1.98};
+    for (int k = 0; k < 5; k++) c->mrt_user[k] = rates ? rates[k] : defaults[k];
+    c->p.eq = equilibrium;
+    c->p.coll = collision;
+    c->gen = equilibrium != LBM_EQ_QCOMPR || collision != LBM_COLL_BGK;
+    set_mrt_constants(c);
+    drop_graphs(c);   // captured launches hold the old parameters and kernel
     return LBM_OK;
 }
 
@@ -562,6 +599,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int T, int ckpt_every, int plane_x, double* l
     if (plane_x < 0 || plane_x >= c->nx) return fail(c, LBM_EINVAL, "plane_x outside the box");
     if (!c->state_set || !c->params_set) return fail(c, LBM_ESTATE, "set parameters and a state first");
     if (c->sr) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint does not support stochastic rounding (LBM_F16S_SR)");
+    if (c->gen) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint supports only the quasi-compressible LBGK model");
     if (c->n_tiles == 0) {
         *loss = 0.0;
         if (dL_dtau) *dL_dtau = 0.0;

@@ -149,6 +149,125 @@ __device__ __forceinline__ void collide(R v[Q], int type, const StepParams& p, R
     }
 }
 
+// ------------------------------------------------------------------- other models
+// D3Q19 moment basis of d'Humieres, Ginzburg, Krafczyk, Lallemand and Luo (2002): row k is
+// a polynomial in the velocity c evaluated on the 19 lattice velocities; every entry is an
+// integer. Rows: rho; e = 19|c|^2 - 30; eps = (21|c|^4 - 53|c|^2 + 24)/2; j_x; q_x = (5|c|^2 -
+// 9) c_x; j_y; q_y; j_z; q_z; 3p_xx = 3c_x^2 - |c|^2; 3pi_xx = (3|c|^2 - 5) 3p_xx; p_ww =
+// c_y^2 - c_z^2; pi_ww = (3|c|^2 - 5) p_ww; p_xy; p_yz; p_xz; m_x = (c_y^2 - c_z^2) c_x;
+// m_y = (c_z^2 - c_x^2) c_y; m_z = (c_x^2 - c_y^2) c_z.
+__host__ __device__ constexpr int mrt_row(int k, int i) {
+    const int x = cx(i), y = cy(i), z = cz(i), cc = x * x + y * y + z * z;
+    return k == 0 ? 1
+         : k == 1 ? 19 * cc - 30
+         : k == 2 ? (21 * cc * cc - 53 * cc + 24) / 2
+         : k == 3 ? x : k == 4 ? (5 * cc - 9) * x
+         : k == 5 ? y : k == 6 ? (5 * cc - 9) * y
+         : k == 7 ? z : k == 8 ? (5 * cc - 9) * z
+         : k == 9 ? 3 * x * x - cc
+         : k == 10 ? (3 * cc - 5) * (3 * x * x - cc)
+         : k == 11 ? y * y - z * z
+         : k == 12 ? (3 * cc - 5) * (y * y - z * z)
+         : k == 13 ? x * y : k == 14 ? y * z : k == 15 ? x * z
+         : k == 16 ? (y * y - z * z) * x
+         : k == 17 ? (z * z - x * x) * y
+         : (x * x - y * y) * z;
+}
+__host__ __device__ constexpr int mrt_norm(int k) {
+    int n = 0;
+    for (int i = 0; i < Q; i++) n += mrt_row(k, i) * mrt_row(k, i);
+    return n;
+}
+
+// Equilibrium of model eq at (rq, u), as f (SHIFT = false; Dq = rq) or as h = f - w
+// (SHIFT = true; Dq = rq - 1): w (Dq + a (3 c.u + 4.5 (c.u)^2 - 1.5 u.u)) with a = rq for the
+// quasi-compressible Eq. 3 and a = 1 for the incompressible Eq. 4.
+template <typename R>
+__device__ __forceinline__ R feq_model(int i, R Dq, R a, R ex, R ey, R ez, R uu15) {
+    const R cu = R(cx(i)) * ex + R(cy(i)) * ey + R(cz(i)) * ez;
+    return R(wgt(i)) * (Dq + a * (R(3) * cu + R(4.5) * cu * cu - uu15));
+}
+
+// Collision of one node for the models other than quasi-compressible LBGK: the
+// incompressible equilibrium (Eq. 4, velocity Eq. 6: u = j + F/2) and MRT (Eq. 8):
+//   m = M (v - v^eq), mG = M G, v* = v^eq + M^T (mrt_a . m + mrt_b . mG),
+// G_i = w_i (3 (c_i - u).F + 9 (c_i.u)(c_i.F)) (Guo forcing in moment space); LBGK is
+//   v* = (1 - omega) v + omega v^eq + (1 - omega/2) G.
+template <typename R, bool SHIFT>
+__device__ __forceinline__ void collide_model(R v[Q], int type, const StepParams& p, R Fx, R Fy, R Fz) {
+    R sum = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        sum += v[i];
+        if (cx(i)) jx += R(cx(i)) * v[i];
+        if (cy(i)) jy += R(cy(i)) * v[i];
+        if (cz(i)) jz += R(cz(i)) * v[i];
+    }
+    const R rho = SHIFT ? R(1) + sum : sum;
+    const R D = sum;
+    const bool inc = p.eq == LBM_EQ_INCOMPR;
+    const R Jx = jx + R(0.5) * Fx, Jy = jy + R(0.5) * Fy, Jz = jz + R(0.5) * Fz;
+    const R ir = inc ? R(1) : R(1) / rho;
+    const R ux = Jx * ir, uy = Jy * ir, uz = Jz * ir;
+    if (type == LBM_INLET || type == LBM_OUTLET) {
+        R ex, ey, ez, Dq, rq;
+        if (type == LBM_INLET) {
+            ex = par<R>(p.u_in[0], p.u_in_f[0]);
+            ey = par<R>(p.u_in[1], p.u_in_f[1]);
+            ez = par<R>(p.u_in[2], p.u_in_f[2]);
+            Dq = D;
+            rq = rho;
+        } else {
+            ex = ux; ey = uy; ez = uz;
+            rq = par<R>(p.rho_out, p.rho_out_f);
+            Dq = SHIFT ? par<R>(p.rho_out - 1.0, p.rho_out_m1_f) : rq;
+        }
+        const R uu15 = R(1.5) * (ex * ex + ey * ey + ez * ez);
+        const R a = inc ? R(1) : rq;
+#pragma unroll
+        for (int i = 0; i < Q; i++) v[i] = feq_model<R>(i, Dq, a, ex, ey, ez, uu15);
+        return;
+    }
+    const R uu15 = R(1.5) * (ux * ux + uy * uy + uz * uz);
+    const R a = inc ? R(1) : rho;
+    const R uF3 = R(3) * (ux * Fx + uy * Fy + uz * Fz);
+    R ve[Q], G[Q];
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        ve[i] = feq_model<R>(i, D, a, ux, uy, uz, uu15);
+        const R cu = R(cx(i)) * ux + R(cy(i)) * uy + R(cz(i)) * uz;
+        const R cF = R(cx(i)) * Fx + R(cy(i)) * Fy + R(cz(i)) * Fz;
+        G[i] = R(wgt(i)) * (R(3) * cF - uF3 + R(9) * cu * cF);
+    }
+    if (p.coll == LBM_COLL_BGK) {
+        const R omega = par<R>(p.omega, p.omega_f), beta = par<R>(p.beta, p.beta_f);
+#pragma unroll
+        for (int i = 0; i < Q; i++) v[i] = v[i] + omega * (ve[i] - v[i]) + beta * G[i];
+        return;
+    }
+    R ms[Q];
+#pragma unroll
+    for (int k = 0; k < Q; k++) {
+        R md = 0, mg = 0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            if (mrt_row(k, i) != 0) {
+                md += R(mrt_row(k, i)) * (v[i] - ve[i]);
+                mg += R(mrt_row(k, i)) * G[i];
+            }
+        }
+        ms[k] = par<R>(p.mrt_a[k], p.mrt_a_f[k]) * md + par<R>(p.mrt_b[k], p.mrt_b_f[k]) * mg;
+    }
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        R acc = ve[i];
+#pragma unroll
+        for (int k = 0; k < Q; k++)
+            if (mrt_row(k, i) != 0) acc += R(mrt_row(k, i)) * ms[k];
+        v[i] = acc;
+    }
+}
+
 // ------------------------------------------------------------ stochastic rounding
 // MurmurHash3's 32-bit finaliser (A. Appleby, public domain): a bijective avalanche mix,
 // used as a counter-based generator keyed by (step counter, node, direction pair).

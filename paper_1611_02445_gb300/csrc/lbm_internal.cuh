@@ -111,6 +111,12 @@ struct StepParams {
     DFConst dfc;   // constants of the double-float FP64 collision
     // FP32 copies for the 4-byte formats (an FP64 -> FP32 conversion runs on the FP64 pipe)
     float omega_f, beta_f, g_f[3], u_in_f[3], rho_out_f, rho_out_m1_f;
+    // collision model (lbm_set_model): equilibrium (LBM_EQ_*) and collision (LBM_COLL_*);
+    // for MRT, moment k relaxes as m*_k = m^eq_k + (1 - s_k)(m_k - m^eq_k) + (1 - s_k/2) mG_k,
+    // kept as mrt_a[k] = (1 - s_k) / |M_k|^2 and mrt_b[k] = (1 - s_k/2) / |M_k|^2
+    int eq, coll;
+    double mrt_a[Q], mrt_b[Q];
+    float mrt_a_f[Q], mrt_b_f[Q];
 };
 
 // A parameter in the arithmetic type R: the FP64 value or its FP32 copy.
@@ -126,6 +132,8 @@ struct lbm_ctx {
     int dtype = LBM_F64;        // storage format (LBM_F64, LBM_F32, LBM_F16S)
     bool native64 = false;      // LBM_F64_NATIVE: FP64 arithmetic throughout
     bool sr = false;            // LBM_F16S_SR: stochastic rounding of the step's stores
+    bool gen = false;           // a collision model other than quasi-compressible LBGK
+    double mrt_user[5] = {1.19, 1.4, 1.2, 1.4, 1.98};   // s_e, s_eps, s_q, s_pi, s_m
     uint32_t* seed = nullptr;   // step counters of the rounding hash, one per copy
     int64_t n_tiles = 0, n_nonsolid = 0;
     cudaStream_t stream = nullptr;

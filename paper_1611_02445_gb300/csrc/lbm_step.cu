@@ -128,7 +128,7 @@ __device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, in
     return odd;
 }
 
-template <int DT, bool VAR, int MODE>
+template <int DT, bool VAR, int MODE, bool GEN>
 __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, uint32_t odd,
                                               typename Store<DT>::T* __restrict__ B, const StepParams& p,
                                               bool has_gf, uint32_t key) {
@@ -157,6 +157,9 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     const R Fy = par<R>(p.g[1], p.g_f[1]), Fz = par<R>(p.g[2], p.g_f[2]);
     if constexpr (MODE != STEP_FULL) {
         // calibration kernels: no collision, the gathered values are stored as they are
+    } else if constexpr (GEN) {
+        // incompressible equilibrium or MRT
+        collide_model<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
     } else if constexpr (DT == LBM_F64 && !VAR) {
         // FP64 storage: double-float collision for fluid nodes, FP64 for the closures
         if (type == LBM_FLUID) collide_df(v, (double)Fx, p.dfc);
@@ -185,7 +188,7 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
 template <int DT> struct StepOcc { static constexpr int CTAS = 4; };
 template <> struct StepOcc<LBM_F64> { static constexpr int CTAS = 2; };
 
-template <int DT, bool VAR, int MODE>
+template <int DT, bool VAR, int MODE, bool GEN>
 __global__ void __launch_bounds__(STEP_THREADS, StepOcc<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
@@ -237,70 +240,83 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         cp_async_commit();
         // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
         cp_async_wait<3>();
-        compute_store<DT, VAR, MODE>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], odd_cur, B, p, has_gf, key);
+        compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], odd_cur, B, p, has_gf, key);
         odd_cur = odd_next;
     }
     cp_async_wait<0>();
 }
 
-template <int DT, bool VAR, int MODE>
+template <int DT, bool VAR, int MODE, bool GEN>
 static int step_grid(int64_t n_groups) {
     static int per_sm = -1, n_sm = 0;
     if (per_sm < 0) {
         int dev = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-        cudaFuncSetAttribute(k_step<DT, VAR, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, VAR, MODE>, STEP_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, VAR, MODE, GEN>, STEP_THREADS,
                                                       sizeof(StepSmem<DT>));
         if (per_sm < 1) per_sm = 1;
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)per_sm * n_sm));
 }
 
-template <int DT, bool VAR, int MODE>
+template <int DT, bool VAR, int MODE, bool GEN>
 static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
-    const int grid = step_grid<DT, VAR, MODE>(c->n_groups);
+    const int grid = step_grid<DT, VAR, MODE, GEN>(c->n_groups);
     // the copy read decides which counter is read and which is advanced
     const int from = A == c->f[0] ? 0 : 1;
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
-    k_step<DT, VAR, MODE><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
+    k_step<DT, VAR, MODE, GEN><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
         (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
         seed_in, seed_out);
     return cudaGetLastError();
 }
 
-template <int MODE>
-static cudaError_t launch_step_mode(lbm_ctx* c, const void* A, void* B) {
+template <int MODE, bool GEN>
+static cudaError_t launch_step_model(lbm_ctx* c, const void* A, void* B) {
     switch (c->dtype) {
         case LBM_F64:
-            return c->native64 ? launch_step_dt<LBM_F64, true, MODE>(c, A, B)
-                               : launch_step_dt<LBM_F64, false, MODE>(c, A, B);
-        case LBM_F32: return launch_step_dt<LBM_F32, false, MODE>(c, A, B);
+            return c->native64 ? launch_step_dt<LBM_F64, true, MODE, GEN>(c, A, B)
+                               : launch_step_dt<LBM_F64, false, MODE, GEN>(c, A, B);
+        case LBM_F32: return launch_step_dt<LBM_F32, false, MODE, GEN>(c, A, B);
         default:
-            return c->sr ? launch_step_dt<LBM_F16S, true, MODE>(c, A, B)
-                         : launch_step_dt<LBM_F16S, false, MODE>(c, A, B);
+            return c->sr ? launch_step_dt<LBM_F16S, true, MODE, GEN>(c, A, B)
+                         : launch_step_dt<LBM_F16S, false, MODE, GEN>(c, A, B);
     }
+}
+
+// The calibration kernels have no collision, so only the fused step has model variants.
+template <int MODE>
+static cudaError_t launch_step_mode(lbm_ctx* c, const void* A, void* B) {
+    if (MODE == STEP_FULL && c->gen) return launch_step_model<STEP_FULL, true>(c, A, B);
+    return launch_step_model<MODE, false>(c, A, B);
 }
 
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B) { return launch_step_kind(c, STEP_FULL, A, B); }
 
 // One-time kernel attributes and occupancy query of the fused step, done outside any
 // stream capture.
-cudaError_t prepare_step(lbm_ctx* c) {
+template <bool GEN>
+static void prepare_model(lbm_ctx* c) {
     switch (c->dtype) {
         case LBM_F64:
-            if (c->native64) step_grid<LBM_F64, true, STEP_FULL>(1);
-            else step_grid<LBM_F64, false, STEP_FULL>(1);
+            if (c->native64) step_grid<LBM_F64, true, STEP_FULL, GEN>(1);
+            else step_grid<LBM_F64, false, STEP_FULL, GEN>(1);
             break;
-        case LBM_F32: step_grid<LBM_F32, false, STEP_FULL>(1); break;
+        case LBM_F32: step_grid<LBM_F32, false, STEP_FULL, GEN>(1); break;
         default:
-            if (c->sr) step_grid<LBM_F16S, true, STEP_FULL>(1);
-            else step_grid<LBM_F16S, false, STEP_FULL>(1);
+            if (c->sr) step_grid<LBM_F16S, true, STEP_FULL, GEN>(1);
+            else step_grid<LBM_F16S, false, STEP_FULL, GEN>(1);
     }
+}
+
+cudaError_t prepare_step(lbm_ctx* c) {
+    if (c->gen) prepare_model<true>(c);
+    else prepare_model<false>(c);
     return cudaGetLastError();
 }
 

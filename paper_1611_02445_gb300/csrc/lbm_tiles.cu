@@ -238,7 +238,7 @@ cudaError_t launch_node_words(lbm_ctx* c) {
 template <int DT>
 __global__ void k_init(typename Store<DT>::T* __restrict__ f0, typename Store<DT>::T* __restrict__ f1,
                        const uint64_t* __restrict__ smask, int64_t n_tiles, double rho0, double ux,
-                       double uy, double uz) {
+                       double uy, double uz, int eq) {
     using T = typename Store<DT>::T;
     const int64_t n = n_tiles * SLOTS;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
@@ -250,7 +250,9 @@ __global__ void k_init(typename Store<DT>::T* __restrict__ f0, typename Store<DT
 #pragma unroll
         for (int i = 0; i < Q; i++) {
             const double cu = cx(i) * ux + cy(i) * uy + cz(i) * uz;
-            const double fe = wgt(i) * rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
+            // Eq. 3, or Eq. 4 for the incompressible model
+            const double fe = eq == LBM_EQ_INCOMPR ? wgt(i) * (rho0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)
+                                                   : wgt(i) * rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
             const T v = solid ? nan_value<DT>() : from_f64<DT>(fe, i);
             f0[(k * Q + i) * SLOTS + s] = v;
             f1[(k * Q + i) * SLOTS + s] = v;
@@ -267,15 +269,15 @@ cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]) {
     switch (c->dtype) {
         case LBM_F64:
             k_init<LBM_F64><<<g, 256, 0, c->stream>>>((double*)c->f[0], (double*)c->f[1], c->smask,
-                                                      c->n_tiles, rho0, u0[0], u0[1], u0[2]);
+                                                      c->n_tiles, rho0, u0[0], u0[1], u0[2], c->p.eq);
             break;
         case LBM_F32:
             k_init<LBM_F32><<<g, 256, 0, c->stream>>>((float*)c->f[0], (float*)c->f[1], c->smask,
-                                                      c->n_tiles, rho0, u0[0], u0[1], u0[2]);
+                                                      c->n_tiles, rho0, u0[0], u0[1], u0[2], c->p.eq);
             break;
         default:
             k_init<LBM_F16S><<<g, 256, 0, c->stream>>>((__half*)c->f[0], (__half*)c->f[1], c->smask,
-                                                       c->n_tiles, rho0, u0[0], u0[1], u0[2]);
+                                                       c->n_tiles, rho0, u0[0], u0[1], u0[2], c->p.eq);
     }
     return cudaGetLastError();
 }
@@ -372,7 +374,8 @@ cudaError_t launch_reduce(lbm_ctx* c, double* d_out) {
 
 // ----------------------------------------------------------------------------------
 // Macroscopic export from the stored post-collision populations: rho = sum f*,
-// u = (sum c f* - F/2)/rho, into dense arrays (already zeroed by the caller).
+// u = (sum c f* - F/2)/rho (Eq. 5; Eq. 6 without the division for the incompressible
+// model), into dense arrays (already zeroed by the caller).
 template <int DT, typename O>
 __global__ void k_macro(const typename Store<DT>::T* __restrict__ f, const uint64_t* __restrict__ smask,
                         const uint32_t* __restrict__ non_empty, const void* __restrict__ gfield,
@@ -401,9 +404,16 @@ __global__ void k_macro(const typename Store<DT>::T* __restrict__ f, const uint6
         }
         const double Fx = gfield ? gfield_at<DT>(gfield, idx) : p.g[0];
         rho[node] = (O)r;
-        u[node] = (O)((jx - 0.5 * Fx) / r);
-        u[N + node] = (O)((jy - 0.5 * p.g[1]) / r);
-        u[2 * N + node] = (O)((jz - 0.5 * p.g[2]) / r);
+        if (p.eq == LBM_EQ_INCOMPR) {
+            // Eq. 6: no division by the density
+            u[node] = (O)(jx - 0.5 * Fx);
+            u[N + node] = (O)(jy - 0.5 * p.g[1]);
+            u[2 * N + node] = (O)(jz - 0.5 * p.g[2]);
+        } else {
+            u[node] = (O)((jx - 0.5 * Fx) / r);
+            u[N + node] = (O)((jy - 0.5 * p.g[1]) / r);
+            u[2 * N + node] = (O)((jz - 0.5 * p.g[2]) / r);
+        }
     }
 }
 

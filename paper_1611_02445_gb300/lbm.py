@@ -58,6 +58,7 @@ def load():
     L.lbm_set_stream.argtypes = [vp, vp]
     L.lbm_set_params.argtypes = [vp, d, pd, vp, i, pd, d]
     L.lbm_init_equilibrium.argtypes = [vp, d, pd]
+    L.lbm_set_model.argtypes = [vp, i, i, pd]
     L.lbm_step.argtypes = [vp, i]
     L.lbm_step_kernel.argtypes = [vp, i, i]
     L.lbm_macroscopic.argtypes = [vp, vp, vp, i, i]
@@ -158,6 +159,13 @@ def lbm_set_params(ctx, tau, g=None, g_field=None, u_in=None, rho_out=1.0):
     return g_field
 
 
+def lbm_set_model(ctx, equilibrium=0, collision=0, rates=None):
+    r = None
+    if rates is not None:
+        r = (ct.c_double * 5)(*[float(x) for x in rates])
+    _check(load().lbm_set_model(ctx, int(equilibrium), int(collision), r), ctx)
+
+
 def lbm_init_equilibrium(ctx, rho0=1.0, u0=None):
     _check(load().lbm_init_equilibrium(ctx, float(rho0), _d3(u0)), ctx)
 
@@ -167,6 +175,8 @@ def lbm_step(ctx, n=1):
 
 
 KERNEL_FULL, KERNEL_PROPAGATE, KERNEL_RW = 0, 1, 2
+EQ_QCOMPR, EQ_INCOMPR = 0, 1
+COLL_BGK, COLL_MRT = 0, 1
 
 
 def lbm_step_kernel(ctx, kind, n=1):
@@ -296,6 +306,9 @@ class Lattice:
 
     def set_params(self, tau, g=None, g_field=None, u_in=None, rho_out=1.0):
         self._keep = lbm_set_params(self.ctx, tau, g, g_field, u_in, rho_out)
+
+    def set_model(self, equilibrium=EQ_QCOMPR, collision=COLL_BGK, rates=None):
+        lbm_set_model(self.ctx, equilibrium, collision, rates)
 
     def init_equilibrium(self, rho0=1.0, u0=None):
         lbm_init_equilibrium(self.ctx, rho0, u0)
