@@ -303,6 +303,38 @@ def run_vessel(args):
     print(json.dumps(out), flush=True)
 
 
+def run_cavity(args):
+    """Lid-driven cavity sweep (the dense cavity3D benchmark of Sec. 4.3, E3/E6): all-fluid
+    N^3 boxes, N = 64 ... 384, walls on every face, the face z = N moving with u = (0.05, 0, 0)
+    (moving-wall bounce-back), tau 0.6, quasi-compressible LBGK; MFLUPS and algorithmic
+    GB/s for every storage format over args.steps steps (no tiles are skipped: eta_t = 1)."""
+    import torch
+    import __graft_entry__
+    from paper_1611_02445_gb300 import lbm
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream()
+    peaks, _ = load_peaks()
+    out = {"workload": "lid-driven cavity N^3, lid z = N at u = (0.05, 0, 0), tau 0.6, LBGK, "
+                       f"{args.steps} timed steps after {args.warmup}", "hbm_peak_gbs": peaks["hbm_gbs"],
+           "sizes": {}}
+    for n in (64, 128, 192, 256, 320, 384):
+        nt = np.ones((n, n, n), np.uint8)
+        row = {}
+        for dtype in ("f64", "f32", "f16s"):
+            with lbm.Lattice(nt, dtype, 0, stream) as L:
+                L.set_params(0.6)
+                L.set_lid(5, (0.05, 0.0, 0.0))
+                L.init_equilibrium()
+                L.step(args.warmup)
+                ms = _timed_steps(L, args.steps, stream)
+                nodes = L.info()["n_nonsolid"]
+            mflups = nodes * args.steps / (ms * 1e-3) / 1e6
+            gbs = mflups * 1e6 * 2 * 19 * BYTES_PER_VALUE[dtype] / 1e9
+            row[dtype] = {"mflups": mflups, "gbs": gbs, "frac": gbs / float(peaks["hbm_gbs"])}
+        out["sizes"][str(n)] = row
+    print(json.dumps(out), flush=True)
+
+
 def run_precision(args):
     """Precision sweep: sphere pack 512^3 (radius 8, porosity 0.35, seed 161102447), tau 0.7,
     g_x 1e-5, periodic; FP64 vs FP32 vs FP16-shifted storage (round to nearest and stochastic
@@ -370,7 +402,7 @@ def main():
     ap.add_argument("--model", default="bgk", choices=list(MODELS),
                     help="collision model: LBGK (Eq. 3, the benchmark), incompressible LBGK (Eq. 4), "
                          "MRT (Eq. 8) with either equilibrium")
-    ap.add_argument("--workload", default="porous", choices=["porous", "poiseuille", "vessel", "precision"],
+    ap.add_argument("--workload", default="porous", choices=["porous", "poiseuille", "vessel", "precision", "cavity"],
                     help="porous is the benchmark line; the others print their own JSON line")
     ap.add_argument("--adj-steps", type=int, default=2000)
     ap.add_argument("--size", type=int, default=256,
@@ -382,7 +414,8 @@ def main():
         run_adjoint_workload(args)
         return
     if args.workload != "porous":
-        {"poiseuille": run_poiseuille, "vessel": run_vessel, "precision": run_precision}[args.workload](args)
+        {"poiseuille": run_poiseuille, "vessel": run_vessel, "precision": run_precision,
+         "cavity": run_cavity}[args.workload](args)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))

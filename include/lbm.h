@@ -134,6 +134,15 @@ enum { LBM_EQ_QCOMPR = 0, LBM_EQ_INCOMPR = 1 };
 enum { LBM_COLL_BGK = 0, LBM_COLL_MRT = 1 };
 lbm_status lbm_set_model(lbm_ctx* ctx, int equilibrium, int collision, const double* rates);
 
+/* Moving wall (the lid of the cavity benchmark, Sec. 4.3): the box face `face` (0: x = -1,
+ * 1: x = nx, 2: y = -1, 3: y = ny, 4: z = -1, 5: z = nz; its axis must not be periodic)
+ * moves with velocity u (3 host doubles). A link whose source lies beyond that face
+ * bounces back from the moving wall (Ladd, J. Fluid Mech. 271, 1994; wall density the
+ * reference density 1): f_i(x) = f*_opp(i)(x) + 6 w_i (c_i . u). face = -1 removes it
+ * (u may then be NULL). LBM_EINVAL for another face, a periodic axis or a non-finite u;
+ * lbm_adjoint does not support a moving wall. */
+lbm_status lbm_set_lid(lbm_ctx* ctx, int face, const double* u);
+
 /* Set both population copies to the equilibrium f^eq(rho0, u0) of the context's model
  * (Eq. 3 by default) at every non-solid node. */
 lbm_status lbm_init_equilibrium(lbm_ctx* ctx, double rho0, const double* u0);

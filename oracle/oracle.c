@@ -249,10 +249,15 @@ void oracle_collide_m(const double f[Q], int type, double tau, const double F[3]
     }
 }
 
-/* oracle_step with a collision model (eq, coll, rates as for oracle_collide_m). */
+/* oracle_step with a collision model (eq, coll, rates as for oracle_collide_m) and an
+ * optional moving wall: lid_face 0..5 = the box face x = -1, x = nx, y = -1, y = ny,
+ * z = -1, z = nz (a non-periodic axis), or -1 for none. A link whose source x - c_i lies
+ * beyond that face bounces back from a wall moving with velocity lid_u (Ladd 1994, the
+ * wall density taken as the reference density 1):
+ *     f_i(x) = f*_opp(i)(x) + 6 w_i (c_i . lid_u). */
 void oracle_step_m(const double* A, double* B, const uint8_t* nt, int nx, int ny, int nz, unsigned periodic,
                    double tau, const double g[3], const double* g_field, const double u_in[3], double rho_out,
-                   int eq, int coll, const double rates[Q], int nthreads);
+                   int eq, int coll, const double rates[Q], int lid_face, const double lid_u[3], int nthreads);
 
 /* Macroscopic fields of either model: u = (sum c f* - F/2) / rho (eq = 0, reading R6) or
  * u = sum c f* - F/2 (eq = 1, Eq. 6). */
@@ -310,9 +315,18 @@ void oracle_step(const double* A, double* B, const uint8_t* nt, int nx, int ny, 
             }
 }
 
+/* Does the link of direction i at node (x,y,z) come from beyond box face `face`? */
+static int beyond_face(int x, int y, int z, int i, int nx, int ny, int nz, int face) {
+    if (face < 0) return 0;
+    const int a = face / 2;
+    const int q = (a == 0 ? x : a == 1 ? y : z) - C[i][a];
+    const int n = a == 0 ? nx : a == 1 ? ny : nz;
+    return (face % 2 == 0) ? q < 0 : q >= n;
+}
+
 void oracle_step_m(const double* A, double* B, const uint8_t* nt, int nx, int ny, int nz, unsigned periodic,
                    double tau, const double g[3], const double* g_field, const double u_in[3], double rho_out,
-                   int eq, int coll, const double rates[Q], int nthreads) {
+                   int eq, int coll, const double rates[Q], int lid_face, const double lid_u[3], int nthreads) {
     long N = (long)nx * ny * nz;
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for schedule(static) num_threads(nthreads)
@@ -324,10 +338,13 @@ void oracle_step_m(const double* A, double* B, const uint8_t* nt, int nx, int ny
                 double f[Q], out[Q], F[3];
                 for (int i = 0; i < Q; i++) {
                     long s;
-                    if (source_node(x, y, z, i, nx, ny, nz, periodic, &s) && nt[s] != SOLID)
+                    if (source_node(x, y, z, i, nx, ny, nz, periodic, &s) && nt[s] != SOLID) {
                         f[i] = A[i * N + s];
-                    else
+                    } else {
                         f[i] = A[opp(i) * N + n];
+                        if (beyond_face(x, y, z, i, nx, ny, nz, lid_face))
+                            f[i] += 6.0 * W[i] * (C[i][0] * lid_u[0] + C[i][1] * lid_u[1] + C[i][2] * lid_u[2]);
+                    }
                 }
                 force_at(n, g, g_field, F);
                 oracle_collide_m(f, nt[n], tau, F, u_in, rho_out, eq, coll, rates, out);

@@ -45,7 +45,7 @@ def load(path):
     L.oracle_step_adj.argtypes = [d, d, d, u8, ci, ci, ci, cu, cd, d, d, d, cd, d, d, d]
     L.oracle_mrt_matrix.argtypes = [d]
     L.oracle_collide_m.argtypes = [d, ci, cd, d, d, cd, ci, ci, d, d]
-    L.oracle_step_m.argtypes = [d, d, u8, ci, ci, ci, cu, cd, d, d, d, cd, ci, ci, d, ci]
+    L.oracle_step_m.argtypes = [d, d, u8, ci, ci, ci, cu, cd, d, d, d, cd, ci, ci, d, ci, d, ci]
     L.oracle_macroscopic_m.argtypes = [d, u8, cl, d, d, ci, d, d]
     L.oracle_loss.argtypes = [d, u8, ci, ci, ci, ci, d, d, d, d, d]
     L.oracle_loss.restype = cd
@@ -316,7 +316,7 @@ def collide_m(f, node_type, tau, F=(0, 0, 0), u_in=(0, 0, 0), rho_out=1.0, eq=EQ
 
 
 def step_m(A, nt, periodic, tau, g=(0, 0, 0), g_field=None, u_in=(0, 0, 0), rho_out=1.0, eq=EQ_QCOMPR,
-           coll=COLL_BGK, rates=None, nthreads=1, out=None):
+           coll=COLL_BGK, rates=None, nthreads=1, out=None, lid_face=-1, lid_u=(0, 0, 0)):
     nt = _u8(nt)
     A = _f64(A)
     nz, ny, nx = nt.shape
@@ -324,17 +324,20 @@ def step_m(A, nt, periodic, tau, g=(0, 0, 0), g_field=None, u_in=(0, 0, 0), rho_
     gf = None if g_field is None else _f64(g_field)
     r = _rates(rates)
     lib().oracle_step_m(_p(A), _p(B), _p(nt, ct.c_uint8), nx, ny, nz, int(periodic), float(tau), _p(_d3(g)),
-                        _p(gf), _p(_d3(u_in)), float(rho_out), int(eq), int(coll), _p(r), int(nthreads))
+                        _p(gf), _p(_d3(u_in)), float(rho_out), int(eq), int(coll), _p(r), int(lid_face),
+                        _p(_d3(lid_u)), int(nthreads))
     return B
 
 
 def run_m(f, nt, steps, periodic, tau, g=(0, 0, 0), g_field=None, u_in=(0, 0, 0), rho_out=1.0, eq=EQ_QCOMPR,
-          coll=COLL_BGK, rates=None, nthreads=1):
-    """``steps`` fused steps of the chosen collision model; returns the final state."""
+          coll=COLL_BGK, rates=None, nthreads=1, lid_face=-1, lid_u=(0, 0, 0)):
+    """``steps`` fused steps of the chosen collision model (and moving wall); returns the
+    final state."""
     A = _f64(f).copy()
     B = A.copy()
     for _ in range(steps):
-        step_m(A, nt, periodic, tau, g, g_field, u_in, rho_out, eq, coll, rates, nthreads, out=B)
+        step_m(A, nt, periodic, tau, g, g_field, u_in, rho_out, eq, coll, rates, nthreads, out=B,
+               lid_face=lid_face, lid_u=lid_u)
         A, B = B, A
     return A
 

@@ -445,6 +445,26 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
     return LBM_OK;
 }
 
+lbm_status lbm_set_lid(lbm_ctx* c, int face, const double* u) {
+    LBM_CHECK_CTX(c);
+    if (face < -1 || face > 5) return fail(c, LBM_EINVAL, "face must be -1 (none) or 0..5");
+    if (face >= 0 && (c->periodic & (1u << (face >> 1)))) return fail(c, LBM_EINVAL, "the lid face's axis is periodic");
+    if (face >= 0 && !finite3(u)) return fail(c, LBM_EINVAL, "u must be finite");
+    const int a = face >> 1;
+    const int sgn = (face & 1) ? -1 : 1;   // the link crosses the face when c_a(i) = sgn
+    for (int i = 0; i < lbm::Q; i++) {
+        const int ci[3] = {lbm::cx(i), lbm::cy(i), lbm::cz(i)};
+        double v = 0.0;
+        if (face >= 0 && ci[a] == sgn) v = 6.0 * lbm::wgt(i) * (ci[0] * u[0] + ci[1] * u[1] + ci[2] * u[2]);
+        c->p.lid_c[i] = v;
+        c->p.lid_c_f[i] = (float)v;
+    }
+    LBM_CUDA(c, lbm::launch_mark_lid(c, face));
+    c->lid_face = face;
+    drop_graphs(c);
+    return LBM_OK;
+}
+
 lbm_status lbm_set_model(lbm_ctx* c, int equilibrium, int collision, const double* rates) {
     LBM_CHECK_CTX(c);
     if (equilibrium != LBM_EQ_QCOMPR && equilibrium != LBM_EQ_INCOMPR)
@@ -600,6 +620,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int T, int ckpt_every, int plane_x, double* l
     if (!c->state_set || !c->params_set) return fail(c, LBM_ESTATE, "set parameters and a state first");
     if (c->sr) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint does not support stochastic rounding (LBM_F16S_SR)");
     if (c->gen) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint supports only the quasi-compressible LBGK model");
+    if (c->lid_face >= 0) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint does not support a moving wall");
     if (c->n_tiles == 0) {
         *loss = 0.0;
         if (dL_dtau) *dL_dtau = 0.0;

@@ -41,6 +41,7 @@ constexpr int TILE = 4;
 constexpr int SLOTS = 64;
 constexpr int NBR = 27;
 constexpr int NBR_STRIDE = 28;   // padded neighbour record: 112 bytes, 16-byte aligned
+constexpr int WORD_LID_BIT = 19;      // compact words: the node lies on the moving-wall face
 constexpr int WORD_TYPE_SHIFT = 20;
 constexpr int WORD_LT_SHIFT = 22;      // compact words: tile within the group (3 bits)
 constexpr int WORD_SLOT_SHIFT = 25;    // compact words: slot in the tile (6 bits)
@@ -117,6 +118,10 @@ struct StepParams {
     int eq, coll;
     double mrt_a[Q], mrt_b[Q];
     float mrt_a_f[Q], mrt_b_f[Q];
+    // moving wall (lbm_set_lid): 6 w_i (c_i . u_lid) for the directions whose links cross
+    // the lid face from a node on it, 0 for the others
+    double lid_c[Q];
+    float lid_c_f[Q];
 };
 
 // A parameter in the arithmetic type R: the FP64 value or its FP32 copy.
@@ -134,6 +139,7 @@ struct lbm_ctx {
     bool sr = false;            // LBM_F16S_SR: stochastic rounding of the step's stores
     bool gen = false;           // a collision model other than quasi-compressible LBGK
     double mrt_user[5] = {1.19, 1.4, 1.2, 1.4, 1.98};   // s_e, s_eps, s_q, s_pi, s_m
+    int lid_face = -1;          // moving box face (lbm_set_lid), -1 for none
     uint32_t* seed = nullptr;   // step counters of the rounding hash, one per copy
     int64_t n_tiles = 0, n_nonsolid = 0;
     cudaStream_t stream = nullptr;
@@ -188,6 +194,7 @@ cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, i
 cudaError_t launch_set_dense(lbm_ctx* c, const double* d_dense);
 cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense);
 cudaError_t launch_gfield_compact(lbm_ctx* c);
+cudaError_t launch_mark_lid(lbm_ctx* c, int face);
 cudaError_t launch_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, double* dL_dg, int dg_on_device,
                            double* dL_dtau, bool* started);
 }  // namespace lbm

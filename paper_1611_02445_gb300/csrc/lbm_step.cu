@@ -155,6 +155,12 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     }
     const R Fx = has_gf ? sm.gf[mslot][t] : par<R>(p.g[0], p.g_f[0]);
     const R Fy = par<R>(p.g[1], p.g_f[1]), Fz = par<R>(p.g[2], p.g_f[2]);
+    if (MODE == STEP_FULL && ((w >> WORD_LID_BIT) & 1u)) {
+        // moving wall: bounced links that cross the lid face gain 6 w_i (c_i . u_lid)
+#pragma unroll
+        for (int i = 1; i < Q; i++)
+            if ((w >> i) & 1u) v[i] += par<R>(p.lid_c[i], p.lid_c_f[i]);
+    }
     if constexpr (MODE != STEP_FULL) {
         // calibration kernels: no collision, the gathered values are stored as they are
     } else if constexpr (GEN) {

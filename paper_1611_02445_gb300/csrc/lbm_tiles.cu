@@ -558,6 +558,37 @@ cudaError_t launch_gfield_compact(lbm_ctx* c) {
     return cudaGetLastError();
 }
 
+// Mark (or clear, face < 0) the compact words of the nodes on a box face: x = 0 (face 0),
+// x = nx - 1 (1), y = 0 (2), y = ny - 1 (3), z = 0 (4), z = nz - 1 (5).
+__global__ void k_mark_lid(uint32_t* __restrict__ fword, const uint32_t* __restrict__ fidx,
+                           const uint32_t* __restrict__ non_empty, int64_t n_nodes, int Tx, int Ty, int nx, int ny,
+                           int nz, int face) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n < n_nodes;
+         n += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t gi = fidx[n];
+        const uint32_t t = non_empty[gi >> 6];
+        const int s = (int)(gi & 63u);
+        const int p[3] = {TILE * (int)(t % (uint32_t)Tx) + (s & 3),
+                          TILE * (int)((t / (uint32_t)Tx) % (uint32_t)Ty) + ((s >> 2) & 3),
+                          TILE * (int)(t / ((uint32_t)Tx * (uint32_t)Ty)) + (s >> 4)};
+        const int dims[3] = {nx, ny, nz};
+        bool on = false;
+        if (face >= 0) {
+            const int a = face >> 1;
+            on = (face & 1) ? p[a] == dims[a] - 1 : p[a] == 0;
+        }
+        const uint32_t w = fword[n] & ~(1u << WORD_LID_BIT);
+        fword[n] = on ? (w | (1u << WORD_LID_BIT)) : w;
+    }
+}
+
+cudaError_t launch_mark_lid(lbm_ctx* c, int face) {
+    if (c->n_nonsolid == 0) return cudaSuccess;
+    k_mark_lid<<<grid_for(c->n_nonsolid, 256), 256, 0, c->stream>>>(c->fword, c->fidx, c->non_empty, c->n_nonsolid,
+                                                                   c->Tx, c->Ty, c->nx, c->ny, c->nz, face);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense) {
     const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
     if (c->dtype == LBM_F64)

@@ -59,6 +59,7 @@ def load():
     L.lbm_set_params.argtypes = [vp, d, pd, vp, i, pd, d]
     L.lbm_init_equilibrium.argtypes = [vp, d, pd]
     L.lbm_set_model.argtypes = [vp, i, i, pd]
+    L.lbm_set_lid.argtypes = [vp, i, pd]
     L.lbm_step.argtypes = [vp, i]
     L.lbm_step_kernel.argtypes = [vp, i, i]
     L.lbm_macroscopic.argtypes = [vp, vp, vp, i, i]
@@ -164,6 +165,10 @@ def lbm_set_model(ctx, equilibrium=0, collision=0, rates=None):
     if rates is not None:
         r = (ct.c_double * 5)(*[float(x) for x in rates])
     _check(load().lbm_set_model(ctx, int(equilibrium), int(collision), r), ctx)
+
+
+def lbm_set_lid(ctx, face=-1, u=None):
+    _check(load().lbm_set_lid(ctx, int(face), _d3(u)), ctx)
 
 
 def lbm_init_equilibrium(ctx, rho0=1.0, u0=None):
@@ -309,6 +314,9 @@ class Lattice:
 
     def set_model(self, equilibrium=EQ_QCOMPR, collision=COLL_BGK, rates=None):
         lbm_set_model(self.ctx, equilibrium, collision, rates)
+
+    def set_lid(self, face=-1, u=None):
+        lbm_set_lid(self.ctx, face, u)
 
     def init_equilibrium(self, rho0=1.0, u0=None):
         lbm_init_equilibrium(self.ctx, rho0, u0)

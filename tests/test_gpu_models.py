@@ -150,3 +150,81 @@ def test_model_switch_drops_captured_graphs():
     fo = O.run(f0, nt, 16, 0b111, 0.8, (1e-5, 0, 0))
     fo = O.run_m(fo, nt, 16, 0b111, 0.8, (1e-5, 0, 0), coll=O.COLL_MRT, rates=O.mrt_rates(0.8))
     assert rel_err(fg, fo, nt) <= 1e-12
+
+
+# ---------------------------------------------------------------- moving wall (lid)
+@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32", "f16s"])
+@pytest.mark.parametrize("coll", [O.COLL_BGK, O.COLL_MRT])
+def test_lid_driven_cavity_matches_oracle(coll, dtype):
+    """Closed box with obstacles, the face z = nz moving along (x, y): 30 steps from
+    perturbed populations, against the oracle's moving-wall bounce-back."""
+    nt = I.random_box(12, 8, 16, p_solid=0.15, seed=41)
+    f0 = I.random_populations(nt, 0.05, seed=42)
+    u_lid = (0.05, 0.02, 0.0)
+    with lbm.Lattice(nt, dtype, 0) as L:
+        L.set_params(0.7)
+        if coll == O.COLL_MRT:
+            L.set_model(O.EQ_QCOMPR, O.COLL_MRT)
+        L.set_lid(5, u_lid)
+        L.set_f(f0)
+        L.step(30)
+        fg = L.get_f()
+    rates = O.mrt_rates(0.7) if coll == O.COLL_MRT else None
+    fo = O.run_m(f0, nt, 30, 0, 0.7, coll=coll, rates=rates, lid_face=5, lid_u=u_lid)
+    err = rel_err(fg, fo, nt)
+    print(f"lid cavity coll {coll} {dtype}: max |f - f_oracle| / w = {err:.3e}")
+    assert err <= TOL[dtype]
+
+
+@pytest.mark.parametrize("face", [0, 1, 2, 3, 4])
+def test_lid_on_every_face(face):
+    nt = I.random_box(8, 12, 8, p_solid=0.1, seed=50 + face)
+    f0 = I.random_populations(nt, 0.05, seed=60 + face)
+    u = (0.02, -0.03, 0.01)
+    with lbm.Lattice(nt, "f64", 0) as L:
+        L.set_params(0.9, (1e-5, 0, 0))
+        L.set_lid(face, u)
+        L.set_f(f0)
+        L.step(12)
+        fg = L.get_f()
+    fo = O.run_m(f0, nt, 12, 0, 0.9, (1e-5, 0, 0), lid_face=face, lid_u=u)
+    assert rel_err(fg, fo, nt) <= 1e-12
+
+
+def test_couette_exact_on_gpu():
+    ny, U, tau = 16, 0.01, 0.8   # slowest mode decays over ~(ny-1)^2 / (pi^2 nu) = 228 steps
+    nt = np.ones((8, ny, 8), np.uint8)
+    nt[:, 0, :] = 0
+    with lbm.Lattice(nt, "f64", 0b101) as L:
+        L.set_params(tau)
+        L.set_lid(3, (U, 0, 0))
+        L.init_equilibrium()
+        L.step(12000)
+        _, u = L.macroscopic()
+    y = np.arange(1, ny, dtype=np.float64)
+    exact = U * (y - 0.5) / (ny - 1)
+    err = np.abs(u[0][:, 1:, :] - exact[None, :, None]).max() / U
+    print(f"Couette on the GPU: max |u - exact| / U = {err:.2e}")
+    assert err <= 1e-10
+
+
+def test_lid_errors_and_removal():
+    nt = I.random_box(8, 8, 8, p_solid=0.1, seed=70)
+    f0 = I.random_populations(nt, 0.05, seed=71)
+    with lbm.Lattice(nt, "f64", 0b001) as L:
+        L.set_params(0.8)
+        for face, u in ((0, (0.1, 0, 0)), (6, (0, 0, 0)), (-2, None), (2, (np.nan, 0, 0))):
+            with pytest.raises(lbm.LBMError) as e:
+                L.set_lid(face, u)
+            assert e.value.status == 1
+        L.set_lid(5, (0.05, 0, 0))
+        L.set_f(f0)
+        with pytest.raises(lbm.LBMError) as e:
+            L.adjoint(4, 2, 3)
+        assert e.value.status == 4
+        L.set_lid(-1)
+        L.set_f(f0)
+        L.step(16)
+        fg = L.get_f()
+    fo = O.run(f0, nt, 16, 0b001, 0.8)
+    assert rel_err(fg, fo, nt) <= 1e-12

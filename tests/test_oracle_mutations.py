@@ -65,9 +65,11 @@ MUTANTS = [
     ("incompressible velocity divides by rho", "? (j[a] + 0.5 * F[a]) / rho : j[a] + 0.5 * F[a];",
      "? (j[a] + 0.5 * F[a]) / rho : (j[a] + 0.5 * F[a]) / rho;"),
     ("incompressible reported velocity", "u[a * N + n] = j[a] - 0.5 * F[a];", "u[a * N + n] = j[a] + 0.5 * F[a];"),
-    ("model step bounce-back", "f[i] = A[opp(i) * N + n];\n                }\n                force_at(n, g, g_field, F);\n"
-     "                oracle_collide_m(", "f[i] = A[i * N + n];\n                }\n                force_at(n, g, g_field, F);\n"
-     "                oracle_collide_m("),
+    ("moving wall term sign", "f[i] += 6.0 * W[i] * (C[i][0] * lid_u[0]", "f[i] -= 6.0 * W[i] * (C[i][0] * lid_u[0]"),
+    ("moving wall term factor", "f[i] += 6.0 * W[i] * (C[i][0] * lid_u[0]", "f[i] += 3.0 * W[i] * (C[i][0] * lid_u[0]"),
+    ("moving wall on the opposite face", "return (face % 2 == 0) ? q < 0 : q >= n;", "return (face % 2 == 1) ? q < 0 : q >= n;"),
+    ("model step bounce-back", "f[i] = A[opp(i) * N + n];\n                        if (beyond_face(",
+     "f[i] = A[i * N + n];\n                        if (beyond_face("),
 ]
 
 
@@ -105,6 +107,7 @@ def _battery():
         ("MRT conservation", lambda: [Mo.test_mrt_conserves_mass_and_adds_force(e) for e in (0, 1)]),
         ("incompressible momentum", lambda: [Mo.test_incompressible_momentum_closed_form(c) for c in (0, 1)]),
         ("magic Poiseuille", lambda: [Mo.test_poiseuille_exact_at_magic_lambda(e, c) for e in (0, 1) for c in (0, 1)]),
+        ("Couette", lambda: Mo.test_couette_exact_with_moving_lid(0.8, 0)),
     ]
     for name, fn in checks:
         try:
