@@ -481,6 +481,15 @@ def main():
     ms_max = float(t.item())
     mass, _ = L.reduce()
     assert np.isfinite(mass)
+    # the FP64 mass/momentum reduction over one population copy (host wall time of the
+    # call, which waits for its result: an upper bound on the kernels' time)
+    red_ms = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0r = time.perf_counter()
+        L.reduce()
+        red_ms.append((time.perf_counter() - t0r) * 1e3)
+    red_ms = min(red_ms)
     if args.kernel != "full":
         args.no_e2e = True
     value = n_nonsolid * args.steps * world / (ms_max * 1e-3) / 1e6
@@ -531,7 +540,11 @@ def main():
                        "l2_policy": "inputs larger than L2 (two population copies of "
                                     f"{info['copy_bytes'] / 1e9:.2f} GB each vs 126 MB L2)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "gpu_launches": args.steps, "clocks": clocks}
+            "roofline": roof, "gpu_launches": args.steps, "clocks": clocks,
+            "reduction": {"ms": red_ms, "bytes": info["copy_bytes"],
+                          "gbs": info["copy_bytes"] / (red_ms * 1e-3) / 1e9,
+                          "what": "lbm_reduce: FP64 mass and momentum over one copy, best of 5 calls, "
+                                  "host wall time including the 32-byte result copy"}}
 
     # end to end through the public API: host node types in, host results out
     if not args.no_e2e:
@@ -587,7 +600,9 @@ FP64_FLOPS_PER_NODE = 331
 # DRAM bytes (read + write) per non-solid node of one step launch, from ncu on the 128^3
 # pack (scaled to a launch by the number of non-solid nodes); None where not captured for
 # the current kernel.
-TRAFFIC_PER_NODE = {"f64": (232.067072e6 + 107.181312e6) / 732512}
+TRAFFIC_PER_NODE = {"f64": (232.097536e6 + 107.664384e6) / 732512,
+                    "f32": (132.618752e6 + 47.519744e6) / 732512,
+                    "f16s": (76.749568e6 + 23.988480e6) / 732512}
 
 if __name__ == "__main__":
     main()

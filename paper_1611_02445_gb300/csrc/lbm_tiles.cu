@@ -4,6 +4,7 @@
 #include <algorithm>
 
 #include "lbm_internal.cuh"
+#include "lbm_df.cuh"
 #include "lbm_store.cuh"
 
 namespace lbm {
@@ -288,6 +289,54 @@ cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]) {
 // on the launch shape, which is fixed per context.
 constexpr int RED_THREADS = 256;
 
+// Moments of one node as doubles: rho (or rho - 1 for the shifted formats, whose f is w + h
+// with sum w = 1) and j. FP64 storage: exact sums of the values in 64-bit fixed point
+// (2^-58), rounded once. FP32 / FP16 storage: the h values are FP32 numbers, summed with
+// Knuth's TwoSum so that each moment is the rounded pair hi + lo (relative error ~2^-48).
+// Either way each moment costs one or two FP64 operations, not 19: FP64 runs on 2 lanes
+// per SM.
+__device__ __forceinline__ float red_add(float a, float b, float& err) {
+    const float sum = __fadd_rn(a, b);
+    const float bb = __fsub_rn(sum, a);
+    err = __fadd_rn(err, __fadd_rn(__fsub_rn(a, __fsub_rn(sum, bb)), __fsub_rn(b, bb)));
+    return sum;
+}
+
+template <int DT>
+__device__ __forceinline__ void node_moments(const typename Store<DT>::T* __restrict__ f, int64_t k, int s,
+                                             double m[4]) {
+    if constexpr (DT == LBM_F64) {
+        int64_t r = 0, jx = 0, jy = 0, jz = 0;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const int64_t q = fix_from_double(f[(k * Q + i) * SLOTS + s]);
+            r += q;
+            if (cx(i)) jx += cx(i) > 0 ? q : -q;
+            if (cy(i)) jy += cy(i) > 0 ? q : -q;
+            if (cz(i)) jz += cz(i) > 0 ? q : -q;
+        }
+        const double sc = 1.0 / (double)(1ull << FIX_SHIFT);
+        m[0] = __ll2double_rn(r) * sc;
+        m[1] = __ll2double_rn(jx) * sc;
+        m[2] = __ll2double_rn(jy) * sc;
+        m[3] = __ll2double_rn(jz) * sc;
+    } else {
+        float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, er = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
+#pragma unroll
+        for (int i = 0; i < Q; i++) {
+            const float h = to_arith<DT>(f[(k * Q + i) * SLOTS + s], i);
+            r = red_add(r, h, er);
+            if (cx(i)) jx = red_add(jx, cx(i) > 0 ? h : -h, ex);
+            if (cy(i)) jy = red_add(jy, cy(i) > 0 ? h : -h, ey);
+            if (cz(i)) jz = red_add(jz, cz(i) > 0 ? h : -h, ez);
+        }
+        m[0] = 1.0 + ((double)r + (double)er);
+        m[1] = (double)jx + (double)ex;
+        m[2] = (double)jy + (double)ey;
+        m[3] = (double)jz + (double)ez;
+    }
+}
+
 template <int DT>
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Store<DT>::T* __restrict__ f,
                                                         const uint64_t* __restrict__ smask,
@@ -300,20 +349,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Store<DT>
         const int64_t k = idx >> 6;
         const int s = (int)(idx & 63);
         if ((smask[k] >> s) & 1) continue;
-        double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            const double v = to_f64<DT>(f[(k * Q + i) * SLOTS + s], i);
-            r += v;
-            jx += cx(i) * v;
-            jy += cy(i) * v;
-            jz += cz(i) * v;
-        }
+        double m[4];
+        node_moments<DT>(f, k, s, m);
         const double Fx = gfield ? gfield_at<DT>(gfield, idx) : p.g[0];
-        acc[0] += r;
-        acc[1] += jx - 0.5 * Fx;
-        acc[2] += jy - 0.5 * p.g[1];
-        acc[3] += jz - 0.5 * p.g[2];
+        acc[0] += m[0];
+        acc[1] += m[1] - 0.5 * Fx;
+        acc[2] += m[2] - 0.5 * p.g[1];
+        acc[3] += m[3] - 0.5 * p.g[2];
     }
     __shared__ double sh[RED_THREADS / 32][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
