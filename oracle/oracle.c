@@ -249,6 +249,64 @@ void oracle_collide_m(const double f[Q], int type, double tau, const double F[3]
     }
 }
 
+/* Zou-He boundary (Zou & He, Phys. Fluids 9, 1997; the D3Q19 form with the transverse
+ * momentum correction of Hecht & Harting, J. Stat. Mech. 2010) at a node on box face
+ * `face` (0: x = 0, 1: x = nx - 1, 2: y = 0, ..., 5: z = nz - 1), whose inward normal is
+ * n = +e_a on the low faces and -e_a on the high ones (a = face / 2). The populations with
+ * c.n > 0 come from outside and are unknown; with B = sum_{c.n=0} f + 2 sum_{c.n<0} f:
+ *   velocity (kind 0, u_b given):  rho = B / (1 - u_b.n), j = rho u_b (eq 0);
+ *                                  j = u_b, rho = B + u_b.n (eq 1, Eq. 6);
+ *   pressure (kind 1, rho_b given, tangential velocity 0): rho = rho_b,
+ *                                  j = rho_b (1 - B / rho_b) n (eq 0); j = (rho_b - B) n (eq 1);
+ * then, j_n = j.n, for the unknown along n:    f_i = f_opp(i) + j_n / 3,
+ * and for each unknown c_i = n + t e_b (t = +-1, b the tangential axis):
+ *   f_i = f_opp(i) + (j_n + t j_b) / 6 - t N_b,  N_b = 1/2 sum_{c.n=0} c_b f - j_b / 3,
+ * which makes the node's density rho and momentum j exactly. out: the completed set. */
+void oracle_zou_he(const double f[Q], int face, int kind, int eq, const double u_b[3], double rho_b,
+                   double out[Q]) {
+    const int a = face / 2;
+    const int sg = (face % 2 == 0) ? 1 : -1;
+    double B = 0.0, T[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < Q; i++) {
+        const int cn = C[i][a] * sg;
+        if (cn == 0) {
+            B += f[i];
+            for (int b = 0; b < 3; b++) T[b] += C[i][b] * f[i];
+        } else if (cn < 0) {
+            B += 2.0 * f[i];
+        }
+    }
+    double rho, j[3];
+    if (kind == 0) {
+        const double un = u_b[a] * sg;
+        rho = eq == 0 ? B / (1.0 - un) : B + un;
+        for (int b = 0; b < 3; b++) j[b] = eq == 0 ? rho * u_b[b] : u_b[b];
+    } else {
+        rho = rho_b;
+        const double jn = eq == 0 ? rho_b * (1.0 - B / rho_b) : rho_b - B;
+        for (int b = 0; b < 3; b++) j[b] = 0.0;
+        j[a] = jn * sg;
+    }
+    const double jn = j[a] * sg;
+    for (int i = 0; i < Q; i++) out[i] = f[i];
+    for (int i = 0; i < Q; i++) {
+        if (C[i][a] * sg <= 0) continue;
+        double v = f[opp(i)];
+        int tang = -1;
+        for (int b = 0; b < 3; b++)
+            if (b != a && C[i][b] != 0) tang = b;
+        if (tang < 0) {
+            v += jn / 3.0;
+        } else {
+            const int t = C[i][tang];
+            const double N = 0.5 * T[tang] - j[tang] / 3.0;
+            v += (jn + t * j[tang]) / 6.0 - t * N;
+        }
+        out[i] = v;
+    }
+    (void)rho;
+}
+
 /* oracle_step with a collision model (eq, coll, rates as for oracle_collide_m) and an
  * optional moving wall: lid_face 0..5 = the box face x = -1, x = nx, y = -1, y = ny,
  * z = -1, z = nz (a non-periodic axis), or -1 for none. A link whose source x - c_i lies
@@ -257,7 +315,8 @@ void oracle_collide_m(const double f[Q], int type, double tau, const double F[3]
  *     f_i(x) = f*_opp(i)(x) + 6 w_i (c_i . lid_u). */
 void oracle_step_m(const double* A, double* B, const uint8_t* nt, int nx, int ny, int nz, unsigned periodic,
                    double tau, const double g[3], const double* g_field, const double u_in[3], double rho_out,
-                   int eq, int coll, const double rates[Q], int lid_face, const double lid_u[3], int nthreads);
+                   int eq, int coll, const double rates[Q], int lid_face, const double lid_u[3], int bc,
+                   int in_face, int out_face, int nthreads);
 
 /* Macroscopic fields of either model: u = (sum c f* - F/2) / rho (eq = 0, reading R6) or
  * u = sum c f* - F/2 (eq = 1, Eq. 6). */
@@ -326,7 +385,8 @@ static int beyond_face(int x, int y, int z, int i, int nx, int ny, int nz, int f
 
 void oracle_step_m(const double* A, double* B, const uint8_t* nt, int nx, int ny, int nz, unsigned periodic,
                    double tau, const double g[3], const double* g_field, const double u_in[3], double rho_out,
-                   int eq, int coll, const double rates[Q], int lid_face, const double lid_u[3], int nthreads) {
+                   int eq, int coll, const double rates[Q], int lid_face, const double lid_u[3], int bc,
+                   int in_face, int out_face, int nthreads) {
     long N = (long)nx * ny * nz;
     if (nthreads < 1) nthreads = 1;
 #pragma omp parallel for schedule(static) num_threads(nthreads)
@@ -347,7 +407,15 @@ void oracle_step_m(const double* A, double* B, const uint8_t* nt, int nx, int ny
                     }
                 }
                 force_at(n, g, g_field, F);
-                oracle_collide_m(f, nt[n], tau, F, u_in, rho_out, eq, coll, rates, out);
+                if (bc == 1 && (nt[n] == INLET || nt[n] == OUTLET)) {
+                    /* Zou-He: complete the unknown populations, then collide as fluid */
+                    double fz[Q];
+                    if (nt[n] == INLET) oracle_zou_he(f, in_face, 0, eq, u_in, 1.0, fz);
+                    else oracle_zou_he(f, out_face, 1, eq, u_in, rho_out, fz);
+                    oracle_collide_m(fz, FLUID, tau, F, u_in, rho_out, eq, coll, rates, out);
+                } else {
+                    oracle_collide_m(f, nt[n], tau, F, u_in, rho_out, eq, coll, rates, out);
+                }
                 for (int i = 0; i < Q; i++) B[i * N + n] = out[i];
             }
 }

@@ -45,7 +45,8 @@ def load(path):
     L.oracle_step_adj.argtypes = [d, d, d, u8, ci, ci, ci, cu, cd, d, d, d, cd, d, d, d]
     L.oracle_mrt_matrix.argtypes = [d]
     L.oracle_collide_m.argtypes = [d, ci, cd, d, d, cd, ci, ci, d, d]
-    L.oracle_step_m.argtypes = [d, d, u8, ci, ci, ci, cu, cd, d, d, d, cd, ci, ci, d, ci, d, ci]
+    L.oracle_step_m.argtypes = [d, d, u8, ci, ci, ci, cu, cd, d, d, d, cd, ci, ci, d, ci, d, ci, ci, ci, ci]
+    L.oracle_zou_he.argtypes = [d, ci, ci, ci, d, cd, d]
     L.oracle_macroscopic_m.argtypes = [d, u8, cl, d, d, ci, d, d]
     L.oracle_loss.argtypes = [d, u8, ci, ci, ci, ci, d, d, d, d, d]
     L.oracle_loss.restype = cd
@@ -316,7 +317,8 @@ def collide_m(f, node_type, tau, F=(0, 0, 0), u_in=(0, 0, 0), rho_out=1.0, eq=EQ
 
 
 def step_m(A, nt, periodic, tau, g=(0, 0, 0), g_field=None, u_in=(0, 0, 0), rho_out=1.0, eq=EQ_QCOMPR,
-           coll=COLL_BGK, rates=None, nthreads=1, out=None, lid_face=-1, lid_u=(0, 0, 0)):
+           coll=COLL_BGK, rates=None, nthreads=1, out=None, lid_face=-1, lid_u=(0, 0, 0), bc=0, in_face=0,
+           out_face=1):
     nt = _u8(nt)
     A = _f64(A)
     nz, ny, nx = nt.shape
@@ -325,19 +327,19 @@ def step_m(A, nt, periodic, tau, g=(0, 0, 0), g_field=None, u_in=(0, 0, 0), rho_
     r = _rates(rates)
     lib().oracle_step_m(_p(A), _p(B), _p(nt, ct.c_uint8), nx, ny, nz, int(periodic), float(tau), _p(_d3(g)),
                         _p(gf), _p(_d3(u_in)), float(rho_out), int(eq), int(coll), _p(r), int(lid_face),
-                        _p(_d3(lid_u)), int(nthreads))
+                        _p(_d3(lid_u)), int(bc), int(in_face), int(out_face), int(nthreads))
     return B
 
 
 def run_m(f, nt, steps, periodic, tau, g=(0, 0, 0), g_field=None, u_in=(0, 0, 0), rho_out=1.0, eq=EQ_QCOMPR,
-          coll=COLL_BGK, rates=None, nthreads=1, lid_face=-1, lid_u=(0, 0, 0)):
+          coll=COLL_BGK, rates=None, nthreads=1, lid_face=-1, lid_u=(0, 0, 0), bc=0, in_face=0, out_face=1):
     """``steps`` fused steps of the chosen collision model (and moving wall); returns the
     final state."""
     A = _f64(f).copy()
     B = A.copy()
     for _ in range(steps):
         step_m(A, nt, periodic, tau, g, g_field, u_in, rho_out, eq, coll, rates, nthreads, out=B,
-               lid_face=lid_face, lid_u=lid_u)
+               lid_face=lid_face, lid_u=lid_u, bc=bc, in_face=in_face, out_face=out_face)
         A, B = B, A
     return A
 
@@ -351,3 +353,15 @@ def macroscopic_m(f, nt, g=(0, 0, 0), g_field=None, eq=EQ_QCOMPR):
     gf = None if g_field is None else _f64(g_field)
     lib().oracle_macroscopic_m(_p(_f64(f)), _p(nt, ct.c_uint8), N, _p(_d3(g)), _p(gf), int(eq), _p(rho), _p(u))
     return rho, u
+
+
+BC_EQUILIBRIUM, BC_ZOU_HE = 0, 1
+
+
+def zou_he(f, face, kind, eq=EQ_QCOMPR, u_b=(0, 0, 0), rho_b=1.0):
+    """Complete the populations of a boundary node on box face ``face`` (Zou-He):
+    kind 0 velocity u_b, kind 1 pressure (density rho_b)."""
+    f = _f64(f).reshape(Q)
+    out = np.zeros(Q)
+    lib().oracle_zou_he(_p(f), int(face), int(kind), int(eq), _p(_d3(u_b)), float(rho_b), _p(out))
+    return out

@@ -256,3 +256,84 @@ def test_lid_at_rest_is_a_plain_wall():
     a = O.run_m(f0, nt, 5, 0, 0.8, lid_face=5, lid_u=(0, 0, 0))
     b = O.run_m(f0, nt, 5, 0, 0.8)
     assert np.array_equal(a, b, equal_nan=True)
+
+
+# -------------------------------------------------------------------- Zou-He
+@pytest.mark.parametrize("eq", [O.EQ_QCOMPR, O.EQ_INCOMPR])
+@pytest.mark.parametrize("face", range(6))
+def test_zou_he_reconstruction_sets_density_and_momentum(face, eq):
+    """The defining property: the completed node has the prescribed momentum (velocity
+    boundary: j = rho u_b, or u_b for the incompressible model) or the prescribed density
+    with no tangential momentum (pressure boundary); known populations are untouched."""
+    rng = np.random.default_rng(face + 10 * eq)
+    a, sg = face // 2, (1 if face % 2 == 0 else -1)
+    known = [i for i in range(Q) if C[i][a] * sg <= 0]
+    for _ in range(5):
+        f = W * (1 + 0.1 * rng.standard_normal(Q))
+        ub = 0.05 * rng.standard_normal(3)
+        out = O.zou_he(f, face, 0, eq, ub)
+        rho, j = out.sum(), C.T @ out
+        assert np.abs(j - (rho * ub if eq == O.EQ_QCOMPR else ub)).max() <= 1e-16
+        assert np.array_equal(out[known], f[known])
+        out = O.zou_he(f, face, 1, eq, rho_b=1.03)
+        j = C.T @ out
+        assert out.sum() == pytest.approx(1.03, abs=1e-15)   # a sum of 19 values
+        assert all(abs(j[b]) <= 1e-16 for b in range(3) if b != a)
+        assert np.array_equal(out[known], f[known])
+
+
+def _duct(nx=32, ny=10, nz=4):
+    """Channel along x: walls y = 0, ny - 1; inlet nodes on x = 0, outlet nodes on x = nx - 1."""
+    nt = np.ones((nz, ny, nx), np.uint8)
+    nt[:, 0, :] = 0
+    nt[:, ny - 1, :] = 0
+    nt[:, 1:ny - 1, 0] = 2
+    nt[:, 1:ny - 1, nx - 1] = 3
+    return nt
+
+
+@pytest.mark.parametrize("eq,coll", [(O.EQ_QCOMPR, O.COLL_BGK), (O.EQ_INCOMPR, O.COLL_MRT)])
+def test_zou_he_channel_boundary_values(eq, coll):
+    """Velocity inlet u = (0.02, 0, 0) on x = 0, pressure outlet rho = 1 on x = nx - 1,
+    periodic in z: after every step the inlet nodes carry exactly u_in and the outlet
+    nodes exactly rho_out (the reconstruction sets them and the collision conserves them)."""
+    nt = _duct()
+    u_in, tau = (0.02, 0.0, 0.0), 0.8
+    rates = O.mrt_rates(tau) if coll == O.COLL_MRT else None
+    f = O.init(nt)
+    inl, outl = nt == 2, nt == 3
+    for _ in range(3):
+        f = O.run_m(f, nt, 40, 0b100, tau, u_in=u_in, rho_out=1.0, eq=eq, coll=coll, rates=rates,
+                    bc=O.BC_ZOU_HE, in_face=0, out_face=1)
+        rho, u = O.macroscopic_m(f, nt, eq=eq)
+        assert np.abs(u[0][inl] - 0.02).max() <= 1e-15 and np.abs(u[1][inl]).max() <= 1e-15
+        assert np.abs(rho[outl] - 1.0).max() <= 1e-15
+    # the flow has developed: the centre-line velocity downstream exceeds the inlet's
+    assert u[0][:, 5, 16].mean() > 0.021
+
+
+@pytest.mark.parametrize("eq", [O.EQ_QCOMPR, O.EQ_INCOMPR])
+@pytest.mark.parametrize("faces", [(0, 1), (3, 2), (4, 5)])
+def test_zou_he_uniform_flow_is_a_fixed_point(faces, eq):
+    """A box periodic across the flow with inlet and outlet planes on opposite faces: the
+    uniform equilibrium f^eq(rho_out, u_in) meets both conditions, so it is a fixed point
+    of the step (the reconstruction returns the equilibrium's own unknowns)."""
+    fi, fo = faces
+    a = fi // 2
+    shape = [8, 8, 8]
+    nt = np.ones(shape, np.uint8)
+    idx_in = [slice(None)] * 3
+    idx_out = [slice(None)] * 3
+    ax = 2 - a                                   # array axis of coordinate a (z, y, x order)
+    idx_in[ax] = 0 if fi % 2 == 0 else -1
+    idx_out[ax] = 0 if fo % 2 == 0 else -1
+    nt[tuple(idx_in)] = 2
+    nt[tuple(idx_out)] = 3
+    periodic = 0b111 & ~(1 << a)
+    u_in = np.zeros(3)
+    u_in[a] = 0.03 if fi % 2 == 0 else -0.03
+    fe = _feq(1.0, u_in, eq)
+    f = np.broadcast_to(fe[:, None, None, None], (Q,) + nt.shape).copy()
+    out = O.run_m(f, nt, 50, periodic, 0.7, u_in=u_in, rho_out=1.0, eq=eq, bc=O.BC_ZOU_HE, in_face=fi,
+                  out_face=fo)
+    assert np.abs(out - f).max() <= 2e-15   # a few ulps of 1/3 after 50 steps

@@ -68,6 +68,10 @@ MUTANTS = [
     ("moving wall term sign", "f[i] += 6.0 * W[i] * (C[i][0] * lid_u[0]", "f[i] -= 6.0 * W[i] * (C[i][0] * lid_u[0]"),
     ("moving wall term factor", "f[i] += 6.0 * W[i] * (C[i][0] * lid_u[0]", "f[i] += 3.0 * W[i] * (C[i][0] * lid_u[0]"),
     ("moving wall on the opposite face", "return (face % 2 == 0) ? q < 0 : q >= n;", "return (face % 2 == 1) ? q < 0 : q >= n;"),
+    ("Zou-He axis term", "v += jn / 3.0;", "v += jn / 6.0;"),
+    ("Zou-He transverse correction sign", "v += (jn + t * j[tang]) / 6.0 - t * N;", "v += (jn + t * j[tang]) / 6.0 + t * N;"),
+    ("Zou-He outgoing sum counted once", "B += 2.0 * f[i];", "B += f[i];"),
+    ("Zou-He velocity density", "rho = eq == 0 ? B / (1.0 - un) : B + un;", "rho = eq == 0 ? B / (1.0 + un) : B + un;"),
     ("model step bounce-back", "f[i] = A[opp(i) * N + n];\n                        if (beyond_face(",
      "f[i] = A[i * N + n];\n                        if (beyond_face("),
 ]
@@ -108,6 +112,9 @@ def _battery():
         ("incompressible momentum", lambda: [Mo.test_incompressible_momentum_closed_form(c) for c in (0, 1)]),
         ("magic Poiseuille", lambda: [Mo.test_poiseuille_exact_at_magic_lambda(e, c) for e in (0, 1) for c in (0, 1)]),
         ("Couette", lambda: Mo.test_couette_exact_with_moving_lid(0.8, 0)),
+        ("Zou-He moments", lambda: [Mo.test_zou_he_reconstruction_sets_density_and_momentum(fc, e)
+                                    for fc in range(6) for e in (0, 1)]),
+        ("Zou-He fixed point", lambda: [Mo.test_zou_he_uniform_flow_is_a_fixed_point((0, 1), e) for e in (0, 1)]),
     ]
     for name, fn in checks:
         try:
