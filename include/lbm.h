@@ -134,6 +134,20 @@ enum { LBM_EQ_QCOMPR = 0, LBM_EQ_INCOMPR = 1 };
 enum { LBM_COLL_BGK = 0, LBM_COLL_MRT = 1 };
 lbm_status lbm_set_model(lbm_ctx* ctx, int equilibrium, int collision, const double* rates);
 
+/* Inlet/outlet scheme (Sec. 2.2). LBM_BC_EQUILIBRIUM (the default): inlet nodes take
+ * f* = f^eq(rho, u_in), outlet nodes f* = f^eq(rho_out, u) (local equilibrium closures).
+ * LBM_BC_ZOU_HE: the paper's Zou-He velocity inlet and constant-pressure outlet (Zou & He,
+ * Phys. Fluids 9, 1997; D3Q19 with the transverse momentum correction of Hecht & Harting,
+ * J. Stat. Mech. 2010): every inlet node lies on box face inlet_face and every outlet node
+ * on outlet_face (0: x = 0, 1: x = nx - 1, 2: y = 0, 3: y = ny - 1, 4: z = 0,
+ * 5: z = nz - 1), whose inward normal n fixes the unknown populations (c.n > 0); they are
+ * completed so that the node has momentum rho u_in (u_in for the incompressible model) or
+ * density rho_out with no tangential velocity, then the node collides as fluid. LBM_EINVAL
+ * for an unknown scheme, a face outside 0..5 or on a periodic axis; lbm_adjoint supports
+ * only the default. */
+enum { LBM_BC_EQUILIBRIUM = 0, LBM_BC_ZOU_HE = 1 };
+lbm_status lbm_set_bc(lbm_ctx* ctx, int scheme, int inlet_face, int outlet_face);
+
 /* Moving wall (the lid of the cavity benchmark, Sec. 4.3): the box face `face` (0: x = -1,
  * 1: x = nx, 2: y = -1, 3: y = ny, 4: z = -1, 5: z = nz; its axis must not be periodic)
  * moves with velocity u (3 host doubles). A link whose source lies beyond that face

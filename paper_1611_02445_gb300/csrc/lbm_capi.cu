@@ -445,6 +445,23 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
     return LBM_OK;
 }
 
+lbm_status lbm_set_bc(lbm_ctx* c, int scheme, int inlet_face, int outlet_face) {
+    LBM_CHECK_CTX(c);
+    if (scheme != LBM_BC_EQUILIBRIUM && scheme != LBM_BC_ZOU_HE) return fail(c, LBM_EINVAL, "unknown boundary scheme");
+    if (scheme == LBM_BC_ZOU_HE) {
+        for (int f : {inlet_face, outlet_face}) {
+            if (f < 0 || f > 5) return fail(c, LBM_EINVAL, "faces must be 0..5");
+            if (c->periodic & (1u << (f >> 1))) return fail(c, LBM_EINVAL, "a Zou-He face lies on a periodic axis");
+        }
+    }
+    c->bc = scheme;
+    c->p.bc = scheme;
+    c->p.zh_face[0] = inlet_face;
+    c->p.zh_face[1] = outlet_face;
+    drop_graphs(c);
+    return LBM_OK;
+}
+
 lbm_status lbm_set_lid(lbm_ctx* c, int face, const double* u) {
     LBM_CHECK_CTX(c);
     if (face < -1 || face > 5) return fail(c, LBM_EINVAL, "face must be -1 (none) or 0..5");
@@ -621,6 +638,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int T, int ckpt_every, int plane_x, double* l
     if (c->sr) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint does not support stochastic rounding (LBM_F16S_SR)");
     if (c->gen) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint supports only the quasi-compressible LBGK model");
     if (c->lid_face >= 0) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint does not support a moving wall");
+    if (c->bc != LBM_BC_EQUILIBRIUM) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint supports only the equilibrium closures");
     if (c->n_tiles == 0) {
         *loss = 0.0;
         if (dL_dtau) *dL_dtau = 0.0;

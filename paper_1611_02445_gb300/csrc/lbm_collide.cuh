@@ -67,9 +67,82 @@ __device__ __forceinline__ void eq_pair(R& a, R& b, R w, R cu, R D, R rho, R uu1
     b = E - O;
 }
 
+// Zou-He completion of an inlet (velocity u_in) or outlet (density rho_out, no tangential
+// velocity) node on box face f = p.zh_face[0 or 1], inward normal n = +e_a (f = 2a) or
+// -e_a (f = 2a + 1). The populations with c.n > 0 came from outside; with
+// B = sum_{c.n=0} f + 2 sum_{c.n<0} f (1 + the same sums of h for the shifted formats,
+// whose weights add up to 1 over these directions):
+//   velocity: rho = B / (1 - u.n), j = rho u (Eq. 3 model); j = u, rho = B + u.n (Eq. 4);
+//   pressure: j = (rho_out - B) n;
+// then the unknown along n is f_opp + j_n / 3 and the unknown n + t e_b is
+// f_opp + (j_n + t j_b) / 6 - t N_b, N_b = 1/2 sum_{c.n=0} c_b f - j_b / 3 (the transverse
+// momentum correction of the D3Q19 form), so that the node has density rho and momentum j.
+template <typename R, bool SHIFT>
+__device__ __forceinline__ void zou_he(R v[Q], int type, const StepParams& p) {
+    const int face = type == LBM_INLET ? p.zh_face[0] : p.zh_face[1];
+    const int a = face >> 1;
+    const int sg = (face & 1) ? -1 : 1;
+    R B = SHIFT ? R(1) : R(0), T0 = 0, T1 = 0, T2 = 0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+        const int cn = (a == 0 ? cx(i) : a == 1 ? cy(i) : cz(i)) * sg;
+        if (cn == 0) {
+            B += v[i];
+            if (cx(i)) T0 += R(cx(i)) * v[i];
+            if (cy(i)) T1 += R(cy(i)) * v[i];
+            if (cz(i)) T2 += R(cz(i)) * v[i];
+        } else if (cn < 0) {
+            B += R(2) * v[i];
+        }
+    }
+    R j0, j1, j2;
+    if (type == LBM_INLET) {
+        const R u0 = par<R>(p.u_in[0], p.u_in_f[0]), u1 = par<R>(p.u_in[1], p.u_in_f[1]),
+                u2 = par<R>(p.u_in[2], p.u_in_f[2]);
+        const R un = (a == 0 ? u0 : a == 1 ? u1 : u2) * R(sg);
+        const bool inc = p.eq == LBM_EQ_INCOMPR;
+        const R rho = inc ? B + un : B / (R(1) - un);
+        const R s = inc ? R(1) : rho;
+        j0 = s * u0;
+        j1 = s * u1;
+        j2 = s * u2;
+    } else {
+        const R jn = par<R>(p.rho_out, p.rho_out_f) - B;
+        j0 = a == 0 ? jn * R(sg) : R(0);
+        j1 = a == 1 ? jn * R(sg) : R(0);
+        j2 = a == 2 ? jn * R(sg) : R(0);
+    }
+    const R jn = (a == 0 ? j0 : a == 1 ? j1 : j2) * R(sg);
+#pragma unroll
+    for (int i = 1; i < Q; i++) {
+        const int cn = (a == 0 ? cx(i) : a == 1 ? cy(i) : cz(i)) * sg;
+        if (cn <= 0) continue;
+        // tangential component of c_i, if any
+        int b = -1, t = 0;
+        if (a != 0 && cx(i) != 0) { b = 0; t = cx(i); }
+        if (a != 1 && cy(i) != 0) { b = 1; t = cy(i); }
+        if (a != 2 && cz(i) != 0) { b = 2; t = cz(i); }
+        R val = v[inv(i)];
+        if (b < 0) {
+            val += jn * R(1.0 / 3.0);
+        } else {
+            const R jb = b == 0 ? j0 : b == 1 ? j1 : j2;
+            const R Tb = b == 0 ? T0 : b == 1 ? T1 : T2;
+            const R N = R(0.5) * Tb - jb * R(1.0 / 3.0);
+            val += (jn + R(t) * jb) * R(1.0 / 6.0) - R(t) * N;
+        }
+        v[i] = val;
+    }
+}
+
 // One node's collision, in place on v[19].
 template <typename R, bool SHIFT>
 __device__ __forceinline__ void collide(R v[Q], int type, const StepParams& p, R Fx, R Fy, R Fz) {
+    if (type != LBM_FLUID && p.bc == LBM_BC_ZOU_HE) {
+        // Zou-He boundary node: complete the unknown populations, then collide as fluid
+        zou_he<R, SHIFT>(v, type, p);
+        type = LBM_FLUID;
+    }
     // moments from pair sums s and differences d of opposite directions
     const R s13 = v[1] + v[3], s24 = v[2] + v[4], s56 = v[5] + v[6], s79 = v[7] + v[9], s810 = v[8] + v[10];
     const R s1114 = v[11] + v[14], s1213 = v[12] + v[13], s1518 = v[15] + v[18], s1617 = v[16] + v[17];
@@ -195,6 +268,10 @@ __device__ __forceinline__ R feq_model(int i, R Dq, R a, R ex, R ey, R ez, R uu1
 //   v* = (1 - omega) v + omega v^eq + (1 - omega/2) G.
 template <typename R, bool SHIFT>
 __device__ __forceinline__ void collide_model(R v[Q], int type, const StepParams& p, R Fx, R Fy, R Fz) {
+    if (type != LBM_FLUID && p.bc == LBM_BC_ZOU_HE) {
+        zou_he<R, SHIFT>(v, type, p);
+        type = LBM_FLUID;
+    }
     R sum = 0, jx = 0, jy = 0, jz = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {

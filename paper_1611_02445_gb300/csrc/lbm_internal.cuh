@@ -122,6 +122,10 @@ struct StepParams {
     // the lid face from a node on it, 0 for the others
     double lid_c[Q];
     float lid_c_f[Q];
+    // boundary scheme of the inlet/outlet nodes (lbm_set_bc): LBM_BC_EQUILIBRIUM or
+    // LBM_BC_ZOU_HE with the box faces of the inlet and the outlet nodes
+    int bc;
+    int zh_face[2];
 };
 
 // A parameter in the arithmetic type R: the FP64 value or its FP32 copy.
@@ -140,6 +144,7 @@ struct lbm_ctx {
     bool gen = false;           // a collision model other than quasi-compressible LBGK
     double mrt_user[5] = {1.19, 1.4, 1.2, 1.4, 1.98};   // s_e, s_eps, s_q, s_pi, s_m
     int lid_face = -1;          // moving box face (lbm_set_lid), -1 for none
+    int bc = 0;                 // inlet/outlet scheme (lbm_set_bc)
     uint32_t* seed = nullptr;   // step counters of the rounding hash, one per copy
     int64_t n_tiles = 0, n_nonsolid = 0;
     cudaStream_t stream = nullptr;

@@ -167,8 +167,14 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
         // incompressible equilibrium or MRT
         collide_model<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
     } else if constexpr (DT == LBM_F64 && !VAR) {
-        // FP64 storage: double-float collision for fluid nodes, FP64 for the closures
-        if (type == LBM_FLUID) collide_df(v, (double)Fx, p.dfc);
+        // FP64 storage: double-float collision for fluid nodes (and Zou-He boundary nodes
+        // once completed), FP64 for the equilibrium closures
+        int ct = type;
+        if (ct != LBM_FLUID && p.bc == LBM_BC_ZOU_HE) {
+            zou_he<double, false>(v, ct, p);
+            ct = LBM_FLUID;
+        }
+        if (ct == LBM_FLUID) collide_df(v, (double)Fx, p.dfc);
         else collide<R, false>(v, type, p, Fx, Fy, Fz);
     } else {
         collide<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);

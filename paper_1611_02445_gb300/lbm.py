@@ -60,6 +60,7 @@ def load():
     L.lbm_init_equilibrium.argtypes = [vp, d, pd]
     L.lbm_set_model.argtypes = [vp, i, i, pd]
     L.lbm_set_lid.argtypes = [vp, i, pd]
+    L.lbm_set_bc.argtypes = [vp, i, i, i]
     L.lbm_step.argtypes = [vp, i]
     L.lbm_step_kernel.argtypes = [vp, i, i]
     L.lbm_macroscopic.argtypes = [vp, vp, vp, i, i]
@@ -167,6 +168,10 @@ def lbm_set_model(ctx, equilibrium=0, collision=0, rates=None):
     _check(load().lbm_set_model(ctx, int(equilibrium), int(collision), r), ctx)
 
 
+def lbm_set_bc(ctx, scheme=0, inlet_face=0, outlet_face=1):
+    _check(load().lbm_set_bc(ctx, int(scheme), int(inlet_face), int(outlet_face)), ctx)
+
+
 def lbm_set_lid(ctx, face=-1, u=None):
     _check(load().lbm_set_lid(ctx, int(face), _d3(u)), ctx)
 
@@ -182,6 +187,7 @@ def lbm_step(ctx, n=1):
 KERNEL_FULL, KERNEL_PROPAGATE, KERNEL_RW = 0, 1, 2
 EQ_QCOMPR, EQ_INCOMPR = 0, 1
 COLL_BGK, COLL_MRT = 0, 1
+BC_EQUILIBRIUM, BC_ZOU_HE = 0, 1
 
 
 def lbm_step_kernel(ctx, kind, n=1):
@@ -314,6 +320,9 @@ class Lattice:
 
     def set_model(self, equilibrium=EQ_QCOMPR, collision=COLL_BGK, rates=None):
         lbm_set_model(self.ctx, equilibrium, collision, rates)
+
+    def set_bc(self, scheme=BC_EQUILIBRIUM, inlet_face=0, outlet_face=1):
+        lbm_set_bc(self.ctx, scheme, inlet_face, outlet_face)
 
     def set_lid(self, face=-1, u=None):
         lbm_set_lid(self.ctx, face, u)

@@ -228,3 +228,79 @@ def test_lid_errors_and_removal():
         fg = L.get_f()
     fo = O.run(f0, nt, 16, 0b001, 0.8)
     assert rel_err(fg, fo, nt) <= 1e-12
+
+
+# -------------------------------------------------------------------- Zou-He
+def _duct(nx=32, ny=10, nz=8):
+    nt = np.ones((nz, ny, nx), np.uint8)
+    nt[:, 0, :] = 0
+    nt[:, ny - 1, :] = 0
+    nt[:, 1:ny - 1, 0] = 2
+    nt[:, 1:ny - 1, nx - 1] = 3
+    return nt
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32", "f16s"])
+@pytest.mark.parametrize("eq,coll", [(O.EQ_QCOMPR, O.COLL_BGK), (O.EQ_INCOMPR, O.COLL_MRT)])
+def test_zou_he_channel_matches_oracle(eq, coll, dtype):
+    nt = _duct()
+    f0 = I.random_populations(nt, 0.02, seed=81)
+    u_in, tau = (0.03, 0.005, 0.0), 0.75
+    with lbm.Lattice(nt, dtype, 0b100) as L:
+        L.set_params(tau, (2e-6, 0, 0), None, u_in, 1.01)
+        L.set_model(eq, coll)
+        L.set_bc(lbm.BC_ZOU_HE, 0, 1)
+        L.set_f(f0)
+        L.step(40)
+        fg = L.get_f()
+        rho_g, u_g = L.macroscopic()
+    rates = O.mrt_rates(tau) if coll == O.COLL_MRT else None
+    fo = O.run_m(f0, nt, 40, 0b100, tau, (2e-6, 0, 0), None, u_in, 1.01, eq=eq, coll=coll, rates=rates,
+                 bc=O.BC_ZOU_HE, in_face=0, out_face=1)
+    err = rel_err(fg, fo, nt)
+    print(f"Zou-He channel ({eq},{coll}) {dtype}: max |f - f_oracle| / w = {err:.3e}")
+    assert err <= TOL[dtype]
+    if dtype == "f64n":
+        # the boundary values the scheme imposes (no force at these checks' precision)
+        assert np.abs(rho_g[nt == 3] - 1.01).max() <= 1e-14
+
+
+@pytest.mark.parametrize("faces", [(0, 1), (3, 2), (4, 5)])
+def test_zou_he_uniform_flow_fixed_point_on_gpu(faces):
+    fi, fo = faces
+    a = fi // 2
+    nt = np.ones((8, 8, 8), np.uint8)
+    ax = 2 - a
+    idx_in, idx_out = [slice(None)] * 3, [slice(None)] * 3
+    idx_in[ax] = 0 if fi % 2 == 0 else -1
+    idx_out[ax] = 0 if fo % 2 == 0 else -1
+    nt[tuple(idx_in)] = 2
+    nt[tuple(idx_out)] = 3
+    u_in = np.zeros(3)
+    u_in[a] = 0.03 if fi % 2 == 0 else -0.03
+    C, _, _ = O.lattice()
+    cu = C @ u_in
+    fe = W * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * (u_in @ u_in))
+    f = np.broadcast_to(fe[:, None, None, None], (19,) + nt.shape).copy()
+    with lbm.Lattice(nt, "f64", 0b111 & ~(1 << a)) as L:
+        L.set_params(0.7, None, None, u_in, 1.0)
+        L.set_bc(lbm.BC_ZOU_HE, fi, fo)
+        L.set_f(f)
+        L.step(50)
+        out = L.get_f()
+    assert np.abs(out - f).max() <= 1e-14
+
+
+def test_zou_he_errors_and_adjoint_refusal():
+    nt = _duct(nz=8)
+    with lbm.Lattice(nt, "f64", 0b100) as L:
+        L.set_params(0.8, None, None, (0.02, 0, 0), 1.0)
+        for args in ((2, 0, 1), (1, 4, 1), (1, 0, 6), (1, -1, 1)):
+            with pytest.raises(lbm.LBMError) as e:
+                L.set_bc(*args)
+            assert e.value.status == 1
+        L.set_bc(lbm.BC_ZOU_HE, 0, 1)
+        L.init_equilibrium()
+        with pytest.raises(lbm.LBMError) as e:
+            L.adjoint(4, 2, 3)
+        assert e.value.status == 4
