@@ -100,6 +100,22 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """The largest of the ranks' values of x (a timed-region duration); the replicas
+    exchange nothing else."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_mflups(nodes_per_rank: int, steps: int, world: int, ms_max: float) -> float:
+    """Whole-job throughput: every rank's node updates over the slowest rank's time."""
+    return nodes_per_rank * steps * world / (ms_max * 1e-3) / 1e6
+
+
 def oracle_baseline(nt, steps_hint: int, budget_s: float, tau, g):
     """Time the FP64 oracle (as it stands) on the host cores on the full geometry."""
     from oracle import oracle as O
@@ -475,10 +491,7 @@ def main():
     clocks = sampler.stop()
     barrier()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = max_over_ranks(ms, world, dev)
     mass, _ = L.reduce()
     assert np.isfinite(mass)
     # the FP64 mass/momentum reduction over one population copy (host wall time of the
@@ -492,7 +505,7 @@ def main():
     red_ms = min(red_ms)
     if args.kernel != "full":
         args.no_e2e = True
-    value = n_nonsolid * args.steps * world / (ms_max * 1e-3) / 1e6
+    value = job_mflups(n_nonsolid, args.steps, world, ms_max)
 
     # roofline of the step kernel: algorithmic bytes B_node = 2 * 19 * n_d per non-solid
     # node update (Eq. 10) over the average launch duration
@@ -566,10 +579,7 @@ def main():
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         lbm.lbm_destroy(ctx)
-        te = torch.tensor([dt], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        dt = float(te.item())
+        dt = max_over_ranks(dt, world, dev)
         d2h = 4 * 8 + rho_h.numel() * 4 + u_h.numel() * 4
         line["e2e"] = {"value": n_nonsolid * args.steps * world / dt / 1e6, "unit": "MFLUPS",
                        "h2d_bytes_per_step": nt.size / args.steps, "d2h_bytes_per_step": d2h / args.steps,
