@@ -325,7 +325,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     c->n_nonsolid = (int64_t)nonsolid;
     {
         // Work units of the step kernel: consecutive tiles, at most GROUP_MAX_TILES of
-        // them and at most GROUP_MAX_NODES non-solid nodes, so that threads map to
+        // them and at most GROUP_MAX_NODES (FP64: GROUP_MAX_NODES_F64) non-solid nodes, so that threads map to
         // non-solid nodes only. Built once on the host from the per-node words.
         std::vector<uint32_t> words((size_t)count * lbm::SLOTS);
         if (count > 0) {
@@ -334,6 +334,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
         }
         std::vector<int4> groups;
         std::vector<uint32_t> fw, fi;
+        const int max_nodes = dtype == LBM_F64 ? lbm::GROUP_MAX_NODES_F64 : lbm::GROUP_MAX_NODES;
         fw.reserve((size_t)nonsolid);
         fi.reserve((size_t)nonsolid);
         int64_t k = 0;
@@ -346,7 +347,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
             while (k < count && g.y < lbm::GROUP_MAX_TILES) {
                 int cnt = 0;
                 for (int sl = 0; sl < lbm::SLOTS; sl++) cnt += (words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) != 0;
-                if (g.w + cnt > lbm::GROUP_MAX_NODES) break;
+                if (g.w + cnt > max_nodes) break;
                 for (int sl = 0; sl < lbm::SLOTS; sl++) {
                     const uint32_t w = words[k * lbm::SLOTS + sl];
                     if ((w >> lbm::WORD_TYPE_SHIFT) == 0) continue;

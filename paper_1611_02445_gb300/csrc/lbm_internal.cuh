@@ -51,7 +51,8 @@ constexpr int GRAPH_STEPS = 16;
 constexpr int STEP_FULL = 0;        // gather, collide, store
 constexpr int STEP_PROPAGATE = 1;   // gather with bounce-back and store ("propagation only")
 constexpr int STEP_RW = 2;          // read and write each node's own values ("read/write only")
-constexpr int GROUP_MAX_NODES = 256;
+constexpr int GROUP_MAX_NODES = 256;       // work-group size of the 4-byte-or-smaller formats
+constexpr int GROUP_MAX_NODES_F64 = 256;   // and of FP64 storage (see the step kernel's CTA shape)
 constexpr int FLAG_HAS_BC = 1;
 // F16S storage scale: h is stored as half(h * 2^12), so |h| in [1.5e-8, 16] is normal.
 constexpr float F16_SCALE = 4096.0f;

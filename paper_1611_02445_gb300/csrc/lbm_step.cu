@@ -27,7 +27,21 @@
 
 namespace lbm {
 
-constexpr int STEP_THREADS = GROUP_MAX_NODES;   // 256: one thread per non-solid node
+// Threads per CTA (one per non-solid node of a work group) and resident CTAs per SM the
+// kernel is compiled for. The 4-byte-or-smaller formats: 4 CTAs of 256 threads (about 46 KB
+// of shared memory each). FP64: 2 CTAs of 256 threads (about 90 KB each, up to 128
+// registers); 3 CTAs of 192 threads would give 18 warps per SM instead of 16, but cap the
+// registers at 96, and the double-float collision then spills and runs 20 % slower.
+template <int DT> struct StepCfg {
+    static constexpr int THREADS = 256;
+    static constexpr int CTAS = 4;
+};
+template <> struct StepCfg<LBM_F64> {
+    static constexpr int THREADS = 256;
+    static constexpr int CTAS = 2;
+};
+static_assert(StepCfg<LBM_F32>::THREADS == GROUP_MAX_NODES && StepCfg<LBM_F64>::THREADS == GROUP_MAX_NODES_F64,
+              "work groups and CTAs must agree");
 constexpr int HDR_SLOTS = 4;
 constexpr int META_SLOTS = 3;
 constexpr int DATA_SLOTS = 2;
@@ -60,9 +74,9 @@ struct StepSmem {
     using G = typename Store<DT>::R;
     int4 hdr[HDR_SLOTS];                                   // {t0, tiles, f0, nodes}
     int32_t nbr[META_SLOTS][GROUP_MAX_TILES][NBR_STRIDE];
-    uint32_t word[META_SLOTS][STEP_THREADS];
-    G gf[META_SLOTS][STEP_THREADS];
-    E data[DATA_SLOTS][Q][STEP_THREADS];
+    uint32_t word[META_SLOTS][StepCfg<DT>::THREADS];
+    G gf[META_SLOTS][StepCfg<DT>::THREADS];
+    E data[DATA_SLOTS][Q][StepCfg<DT>::THREADS];
 };
 
 __device__ __forceinline__ void issue_hdr(int4* hdr, int64_t grp, int64_t n_groups, const int4* __restrict__ groups) {
@@ -197,11 +211,9 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
 
 // Resident CTAs per SM the kernel is compiled for: shared memory allows 4 CTAs of the
 // 4-byte formats (about 46 KB each) and 2 of FP64 (about 88 KB each); registers match.
-template <int DT> struct StepOcc { static constexpr int CTAS = 4; };
-template <> struct StepOcc<LBM_F64> { static constexpr int CTAS = 2; };
 
 template <int DT, bool VAR, int MODE, bool GEN>
-__global__ void __launch_bounds__(STEP_THREADS, StepOcc<DT>::CTAS)
+__global__ void __launch_bounds__(StepCfg<DT>::THREADS, StepCfg<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
        const void* __restrict__ gfield_c, int64_t n_groups, StepParams p, const uint32_t* __restrict__ seed_in,
@@ -267,7 +279,7 @@ static int step_grid(int64_t n_groups) {
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, VAR, MODE, GEN>, STEP_THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, VAR, MODE, GEN>, StepCfg<DT>::THREADS,
                                                       sizeof(StepSmem<DT>));
         if (per_sm < 1) per_sm = 1;
     }
@@ -282,7 +294,7 @@ static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     const int from = A == c->f[0] ? 0 : 1;
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
-    k_step<DT, VAR, MODE, GEN><<<grid, STEP_THREADS, sizeof(StepSmem<DT>), c->stream>>>(
+    k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, sizeof(StepSmem<DT>), c->stream>>>(
         (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
         seed_in, seed_out);
     return cudaGetLastError();
