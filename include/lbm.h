@@ -74,7 +74,7 @@ typedef enum {
  *                   part of a saved state. lbm_adjoint returns LBM_EUNSUPPORTED for it.
  * lbm_get_f and lbm_get_f_box return f = w_i + h_i in FP64, lbm_set_f rounds f - w_i
  * to the stored format, and lbm_save_state copies the stored values as they are.
- * Inlet/outlet nodes use the FP64 arithmetic in both FP64 modes. */
+ * The equilibrium inlet/outlet closures run in FP64 in both FP64 modes. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F64_NATIVE = 3, LBM_F16S_SR = 4 } lbm_dtype;
 
 enum { LBM_SOLID = 0, LBM_FLUID = 1, LBM_INLET = 2, LBM_OUTLET = 3 };
@@ -162,7 +162,9 @@ lbm_status lbm_set_lid(lbm_ctx* ctx, int face, const double* u);
 lbm_status lbm_init_equilibrium(lbm_ctx* ctx, double rho0, const double* u0);
 
 /* Advance n >= 0 time steps: n launches of the fused step kernel, each reading the
- * current copy and writing the other, then swapping them (Sec. 3.1). */
+ * current copy and writing the other, then swapping them (Sec. 3.1). Runs of 16 steps
+ * are replayed from a CUDA graph captured on first use (and again after any call that
+ * changes parameters, model, boundary scheme or lid). */
 lbm_status lbm_step(lbm_ctx* ctx, int n);
 
 /* The paper's calibration kernels (Sec. 4.1), which bound what the fused step can reach
@@ -176,8 +178,9 @@ lbm_status lbm_step_kernel(lbm_ctx* ctx, int kind, int n);
 
 /* Density and velocity from the stored post-collision populations f*:
  * rho = sum_i f*_i, u = (sum_i c_i f*_i - F/2) / rho (Eq. 5 with the half-force shift of
- * Guo forcing; Eq. 6, without the division, for LBM_EQ_INCOMPR); 0 at solid nodes. rho: nx*ny*nz values, u: 3*nx*ny*nz values, dense,
- * double if out_f64 else float; device pointers if on_device, else host. */
+ * Guo forcing; Eq. 6, without the division, for LBM_EQ_INCOMPR); 0 at solid nodes.
+ * rho: nx*ny*nz values, u: 3*nx*ny*nz values, dense, double if out_f64 else float;
+ * device pointers if on_device, else host. */
 lbm_status lbm_macroscopic(lbm_ctx* ctx, void* rho, void* u, int out_f64, int on_device);
 
 /* Global invariants over non-solid nodes, accumulated in FP64 with warp shuffles and a
@@ -212,8 +215,9 @@ lbm_status lbm_set_f(lbm_ctx* ctx, const double* f_dense);
  * precision (FP64 for LBM_F64, FP32 otherwise). Device memory: (ceil(T/ckpt_every) +
  * min(ckpt_every, T)) population copies plus two adjoint copies; if it cannot be
  * allocated the call returns LBM_ENOMEM before any work and the state is unchanged.
- * A context of format LBM_F16S_SR returns LBM_EUNSUPPORTED (its recompute would not
- * reproduce the forward's random rounding without storing the counter per segment). */
+ * LBM_EUNSUPPORTED for a context of format LBM_F16S_SR (its recompute would not
+ * reproduce the forward's random rounding without storing the counter per segment),
+ * with a model other than quasi-compressible LBGK, a moving wall or Zou-He boundaries. */
 lbm_status lbm_adjoint(lbm_ctx* ctx, int T, int ckpt_every, int plane_x, double* loss, double* dL_dg,
                        int dL_dg_on_device, double* dL_dtau);
 
