@@ -29,7 +29,8 @@ namespace lbm {
 
 // Threads per CTA (one per non-solid node of a work group) and resident CTAs per SM the
 // kernel is compiled for. The 4-byte-or-smaller formats: 4 CTAs of 256 threads (about 46 KB
-// of shared memory each). FP64: 2 CTAs of 256 threads (about 90 KB each, up to 128
+// of shared memory each; 8 CTAs of 128 threads, the same warps with half the work per
+// group, run 25 % slower). FP64: 2 CTAs of 256 threads (about 90 KB each, up to 128
 // registers); 3 CTAs of 192 threads would give 18 warps per SM instead of 16, but cap the
 // registers at 96, and the double-float collision then spills and runs 20 % slower.
 template <int DT> struct StepCfg {
