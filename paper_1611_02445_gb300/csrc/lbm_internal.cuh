@@ -43,9 +43,10 @@ constexpr int NBR = 27;
 constexpr int NBR_STRIDE = 28;   // padded neighbour record: 112 bytes, 16-byte aligned
 constexpr int WORD_LID_BIT = 19;      // compact words: the node lies on the moving-wall face
 constexpr int WORD_TYPE_SHIFT = 20;
-constexpr int WORD_LT_SHIFT = 22;      // compact words: tile within the group (3 bits)
-constexpr int WORD_SLOT_SHIFT = 25;    // compact words: slot in the tile (6 bits)
-constexpr int GROUP_MAX_TILES = 8;
+constexpr int WORD_LT_SHIFT = 22;      // compact words: tile within the group (4 bits)
+constexpr int WORD_LT_MASK = 15;
+constexpr int WORD_SLOT_SHIFT = 26;    // compact words: slot in the tile (6 bits)
+constexpr int GROUP_MAX_TILES = 16;
 constexpr int GRAPH_STEPS = 16;
 // kernel kinds: the fused step and the paper's two calibration kernels (Sec. 4.1)
 constexpr int STEP_FULL = 0;        // gather, collide, store

@@ -1,6 +1,6 @@
 // lbm_step.cu -- the fused collide-and-stream step kernel (Sec. 3.4, Algorithm 2).
 //
-// Work unit: a group of up to 8 consecutive kept tiles holding up to 256 non-solid
+// Work unit: a group of up to 16 consecutive kept tiles holding up to 256 non-solid
 // nodes, one thread per non-solid node (solid slots of a tile get no thread, so no warp
 // lane idles on them). Persistent CTAs walk the groups b, b + G, b + 2G, ... with a
 // software pipeline, so that while a group is computed the next group's gathers are
@@ -16,8 +16,10 @@
 //             bounce-back, Sec. 2.2; propagation only between non-solid nodes,
 //             Sec. 3.4): 19 cp.async copies per node into a 2-slot staging ring, so
 //             the bytes in flight do not occupy registers;
-//   compute(g) moments, inlet/outlet closures or LBGK + Guo collision (Eq. 2, 3, 7)
-//             and coalesced stores of all 19 results into the other copy.
+//   compute(g) the moving-wall term of lid links, inlet/outlet closures (equilibrium,
+//             or Zou-He completion then collision), the collision (LBGK + Guo, Eq. 2, 3,
+//             7; or the incompressible / MRT models) and coalesced stores of all 19
+//             results into the other copy.
 // Solid nodes issue no copies and no stores.
 #include <algorithm>
 
@@ -30,7 +32,7 @@ namespace lbm {
 // Threads per CTA (one per non-solid node of a work group) and resident CTAs per SM the
 // kernel is compiled for. The 4-byte-or-smaller formats: 4 CTAs of 256 threads (about 46 KB
 // of shared memory each; 8 CTAs of 128 threads, the same warps with half the work per
-// group, run 25 % slower). FP64: 2 CTAs of 256 threads (about 90 KB each, up to 128
+// group, run 25 % slower, and 2 CTAs of 512 threads 1-2 % slower). FP64: 2 CTAs of 256 threads (about 90 KB each, up to 128
 // registers); 3 CTAs of 192 threads would give 18 warps per SM instead of 16, but cap the
 // registers at 96, and the double-float collision then spills and runs 20 % slower.
 template <int DT> struct StepCfg {
@@ -115,7 +117,7 @@ __device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, in
     const uint32_t w = sm.word[mslot][t];
     uint32_t odd = 0;
     if (((w >> WORD_TYPE_SHIFT) & 3u) == LBM_SOLID) return 0;
-    const int lt = (int)((w >> WORD_LT_SHIFT) & 7u), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
+    const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
     const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
 #pragma unroll
@@ -153,7 +155,7 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     const uint32_t w = sm.word[mslot][t];
     const int type = (int)((w >> WORD_TYPE_SHIFT) & 3u);
     if (type == LBM_SOLID) return;
-    const int lt = (int)((w >> WORD_LT_SHIFT) & 7u), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
+    const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     R v[Q];
 #pragma unroll
     for (int i = 0; i < Q; i++) {
