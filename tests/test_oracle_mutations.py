@@ -131,19 +131,27 @@ def _compile(text, out):
                     "-w", out + ".c", "-o", out, "-lm"], check=True)
 
 
+def _run_mutant(args):
+    k, name, text, td = args
+    so = os.path.join(td, f"m{k}.so")
+    _compile(text, so)
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), so], cwd=ROOT,
+                       capture_output=True, text=True, timeout=300)
+    caught = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else f"exit {r.returncode}"
+    return name, r.returncode == 0 and caught == "SURVIVED"
+
+
 def test_every_mutant_is_caught():
+    from concurrent.futures import ThreadPoolExecutor
     src = open(SRC).read()
-    survivors = []
+    for name, old, _ in MUTANTS:
+        assert src.count(old) == 1, f"mutation site not unique: {name}"
     with tempfile.TemporaryDirectory() as td:
-        for k, (name, old, new) in enumerate(MUTANTS):
-            assert src.count(old) == 1, f"mutation site not unique: {name}"
-            so = os.path.join(td, f"m{k}.so")
-            _compile(src.replace(old, new), so)
-            r = subprocess.run([sys.executable, os.path.abspath(__file__), so], cwd=ROOT,
-                               capture_output=True, text=True, timeout=300)
-            caught = r.stdout.strip().splitlines()[-1] if r.stdout.strip() else f"exit {r.returncode}"
-            if r.returncode == 0 and caught == "SURVIVED":
-                survivors.append(name)
+        jobs = [(k, name, src.replace(old, new), td) for k, (name, old, new) in enumerate(MUTANTS)]
+        # each mutant compiles and runs in its own child process: run them side by side
+        with ThreadPoolExecutor(max_workers=max(1, min(8, os.cpu_count() or 1))) as ex:
+            results = list(ex.map(_run_mutant, jobs))
+    survivors = [name for name, survived in results if survived]
     assert not survivors, f"mutants not caught by any pin: {survivors}"
 
 
