@@ -10,7 +10,7 @@
 // and dL/dF(x), dL/dtau accumulate (dC/dF)^T lambda and (dC/dtau)^T lambda.
 // One adjoint kernel per step reads s_t with the forward gather and mu_{t+1} with the
 // transposed gather (both pull-shaped) and writes mu_t. Gradients accumulate in FP64:
-// per node for F_x, per block for tau (each block always owns the same tiles, so the
+// per node for F_x, per block for tau (each block always owns the same nodes, so the
 // sums are deterministic).
 #include <algorithm>
 #include <cmath>
@@ -21,8 +21,7 @@
 
 namespace lbm {
 
-constexpr int ADJ_TILES = 2;
-constexpr int ADJ_THREADS = ADJ_TILES * SLOTS;
+constexpr int ADJ_THREADS = 128;
 constexpr int LOSS_THREADS = 256;
 
 template <int DT> using Arith = typename Store<DT>::R;
@@ -203,30 +202,31 @@ __device__ __forceinline__ R collide_adjoint(const R v[Q], const R lam[Q], int t
 }
 
 // One reverse step: mu_out = J_C(G s_t)^T lambda_{t+1}, lambda_{t+1} = G^T mu_in (or
-// mu_in itself when direct, for the seed of the last step).
+// mu_in itself when direct, for the seed of the last step). One thread per non-solid
+// node of the compact node list (the step kernel's per-node words and slot indices), so
+// no lane idles on a solid slot; neighbour tile ranks come through the read-only cache.
+// Block b always owns the nodes [b ADJ_THREADS, (b + 1) ADJ_THREADS): its dL/dtau
+// partial is deterministic.
 template <int DT>
 __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const typename Store<DT>::T* __restrict__ st,
                                                          const Arith<DT>* __restrict__ mu_in, int direct,
                                                          Arith<DT>* __restrict__ mu_out,
                                                          const int32_t* __restrict__ nbr,
-                                                         const uint32_t* __restrict__ nword,
-                                                         const void* __restrict__ gfield, int64_t n_tiles,
+                                                         const uint32_t* __restrict__ fword,
+                                                         const uint32_t* __restrict__ fidx,
+                                                         const void* __restrict__ gfield, int64_t n_nodes,
                                                          StepParams p, double* __restrict__ gbar,
                                                          double* __restrict__ tau_part) {
     using R = Arith<DT>;
-    __shared__ int64_t s_base[ADJ_TILES][NBR];
     __shared__ double s_tau[ADJ_THREADS / 32];
-    const int lt = threadIdx.x >> 6, s = threadIdx.x & 63;
-    const int64_t k = (int64_t)blockIdx.x * ADJ_TILES + lt;
-    if (s < NBR) {
-        const int64_t nk = k < n_tiles ? (int64_t)nbr[k * NBR_STRIDE + s] : -1;
-        s_base[lt][s] = nk >= 0 ? nk * (Q * SLOTS) : -1;
-    }
-    __syncthreads();
+    const int64_t n = (int64_t)blockIdx.x * ADJ_THREADS + threadIdx.x;
     double taubar = 0.0;
-    const uint32_t w = k < n_tiles ? nword[k * SLOTS + s] : 0u;
-    const int type = (int)(w >> WORD_TYPE_SHIFT);
-    if (type != LBM_SOLID) {
+    if (n < n_nodes) {
+        const uint32_t w = __ldg(fword + n);
+        const uint32_t gi = __ldg(fidx + n);
+        const int type = (int)((w >> WORD_TYPE_SHIFT) & 3u);
+        const int64_t k = gi >> 6;
+        const int s = (int)(gi & 63u);
         const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
         const int64_t own = k * (Q * SLOTS);
         R v[Q], lam[Q], mu[Q];
@@ -238,20 +238,21 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const typename Store<DT
             const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
             const int ss = (sx & 3) | ((sy & 3) << 2) | ((sz & 3) << 4);
             const bool bounce = (w >> i) & 1;
-            const int64_t src = bounce ? own + inv(i) * SLOTS + s : s_base[lt][nb] + i * SLOTS + ss;
+            const int64_t base = bounce ? 0 : (nb == 13 ? own : (int64_t)__ldg(nbr + k * NBR_STRIDE + nb) * (Q * SLOTS));
+            const int64_t src = bounce ? own + inv(i) * SLOTS + s : base + i * SLOTS + ss;
             v[i] = to_arith<DT>(st[src], i);
             if (direct) {
                 lam[inv(i)] = mu_in[own + inv(i) * SLOTS + s];
             } else {
-                lam[inv(i)] = bounce ? mu_in[own + i * SLOTS + s] : mu_in[s_base[lt][nb] + inv(i) * SLOTS + ss];
+                lam[inv(i)] = bounce ? mu_in[own + i * SLOTS + s] : mu_in[base + inv(i) * SLOTS + ss];
             }
         }
-        const R Fx = gfield ? (R)gfield_at<DT>(gfield, k * SLOTS + s) : par<R>(p.g[0], p.g_f[0]);
+        const R Fx = gfield ? (R)gfield_at<DT>(gfield, (int64_t)gi) : par<R>(p.g[0], p.g_f[0]);
         const R Fb = collide_adjoint<R, Store<DT>::SHIFT>(v, lam, type, p, Fx, par<R>(p.g[1], p.g_f[1]),
                                                           par<R>(p.g[2], p.g_f[2]), mu, taubar);
 #pragma unroll
         for (int i = 0; i < Q; i++) mu_out[own + i * SLOTS + s] = mu[i];
-        gbar[k * SLOTS + s] += (double)Fb;
+        gbar[gi] += (double)Fb;
     }
     for (int o = 16; o > 0; o >>= 1) taubar += __shfl_down_sync(0xffffffffu, taubar, o);
     if ((threadIdx.x & 31) == 0) s_tau[threadIdx.x >> 5] = taubar;
@@ -302,7 +303,7 @@ cudaError_t run_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, dou
     const int n_ck = (T + K - 1) / K;
     const int seg_len = std::min(K, T);
     const size_t mu_bytes = (size_t)c->n_tiles * Q * SLOTS * sizeof(R);
-    const int adj_blocks = (int)((c->n_tiles + ADJ_TILES - 1) / ADJ_TILES);
+    const int adj_blocks = (int)std::max<int64_t>(1, (c->n_nonsolid + ADJ_THREADS - 1) / ADJ_THREADS);
     const int nbl = (int)std::max<int64_t>(1, std::min<int64_t>((n_slots + LOSS_THREADS - 1) / LOSS_THREADS, 152 * 4));
     const size_t N = (size_t)c->nx * c->ny * c->nz;
     // every buffer is allocated before any work, so that a failed allocation leaves the
@@ -370,7 +371,8 @@ cudaError_t run_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, dou
         for (int t = t1 - 1; t >= t0; t--) {
             k_adjoint<DT><<<adj_blocks, ADJ_THREADS, 0, c->stream>>>(
                 reinterpret_cast<const TT*>(sb + copy * (t - t0)), mu[mcur], direct ? 1 : 0, mu[1 - mcur], c->nbr,
-                c->nword, c->gfield, c->n_tiles, c->p, static_cast<double*>(gbar.p), static_cast<double*>(taup.p));
+                c->fword, c->fidx, c->gfield, c->n_nonsolid, c->p, static_cast<double*>(gbar.p),
+                static_cast<double*>(taup.p));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             mcur ^= 1;
             direct = false;

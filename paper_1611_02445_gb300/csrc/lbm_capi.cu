@@ -324,7 +324,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
     c->n_nonsolid = (int64_t)nonsolid;
     {
-        // Work units of the step kernel: consecutive tiles, at most GROUP_MAX_TILES of
+        // Work units of the step kernel: consecutive tiles, at most GROUP_MAX_TILES_* of
         // them and at most GROUP_MAX_NODES (FP64: GROUP_MAX_NODES_F64) non-solid nodes, so that threads map to
         // non-solid nodes only. Built once on the host from the per-node words.
         std::vector<uint32_t> words((size_t)count * lbm::SLOTS);
@@ -335,6 +335,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
         std::vector<int4> groups;
         std::vector<uint32_t> fw, fi;
         const int max_nodes = dtype == LBM_F64 ? lbm::GROUP_MAX_NODES_F64 : lbm::GROUP_MAX_NODES;
+        const int max_tiles = dtype == LBM_F64 ? lbm::GROUP_MAX_TILES_F64 : lbm::GROUP_MAX_TILES_4B;
         fw.reserve((size_t)nonsolid);
         fi.reserve((size_t)nonsolid);
         int64_t k = 0;
@@ -344,7 +345,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
             g.y = 0;
             g.z = (int)fw.size();
             g.w = 0;
-            while (k < count && g.y < lbm::GROUP_MAX_TILES) {
+            while (k < count && g.y < max_tiles) {
                 int cnt = 0;
                 for (int sl = 0; sl < lbm::SLOTS; sl++) cnt += (words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) != 0;
                 if (g.w + cnt > max_nodes) break;

@@ -46,7 +46,8 @@ constexpr int WORD_TYPE_SHIFT = 20;
 constexpr int WORD_LT_SHIFT = 22;      // compact words: tile within the group (4 bits)
 constexpr int WORD_LT_MASK = 15;
 constexpr int WORD_SLOT_SHIFT = 26;    // compact words: slot in the tile (6 bits)
-constexpr int GROUP_MAX_TILES = 16;
+constexpr int GROUP_MAX_TILES_F64 = 16;   // tiles per work group: FP64 storage
+constexpr int GROUP_MAX_TILES_4B = 8;     // and the 4-byte-or-smaller formats
 constexpr int GRAPH_STEPS = 16;
 // kernel kinds: the fused step and the paper's two calibration kernels (Sec. 4.1)
 constexpr int STEP_FULL = 0;        // gather, collide, store

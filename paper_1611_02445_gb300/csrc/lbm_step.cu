@@ -1,6 +1,6 @@
 // lbm_step.cu -- the fused collide-and-stream step kernel (Sec. 3.4, Algorithm 2).
 //
-// Work unit: a group of up to 16 consecutive kept tiles holding up to 256 non-solid
+// Work unit: a group of up to 16 (FP64) or 8 consecutive kept tiles holding up to 256 non-solid
 // nodes, one thread per non-solid node (solid slots of a tile get no thread, so no warp
 // lane idles on them). Persistent CTAs walk the groups b, b + G, b + 2G, ... with a
 // software pipeline, so that while a group is computed the next group's gathers are
@@ -22,6 +22,7 @@
 //             results into the other copy.
 // Solid nodes issue no copies and no stores.
 #include <algorithm>
+#include <cstddef>
 
 #include "lbm_collide.cuh"
 #include "lbm_internal.cuh"
@@ -38,10 +39,12 @@ namespace lbm {
 template <int DT> struct StepCfg {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 4;
+    static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
 };
 template <> struct StepCfg<LBM_F64> {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 2;
+    static constexpr int MAX_TILES = GROUP_MAX_TILES_F64;
 };
 static_assert(StepCfg<LBM_F32>::THREADS == GROUP_MAX_NODES && StepCfg<LBM_F64>::THREADS == GROUP_MAX_NODES_F64,
               "work groups and CTAs must agree");
@@ -76,10 +79,12 @@ struct StepSmem {
     using E = typename Staged<DT>::E;
     using G = typename Store<DT>::R;
     int4 hdr[HDR_SLOTS];                                   // {t0, tiles, f0, nodes}
-    int32_t nbr[META_SLOTS][GROUP_MAX_TILES][NBR_STRIDE];
+    int32_t nbr[META_SLOTS][StepCfg<DT>::MAX_TILES][NBR_STRIDE];
     uint32_t word[META_SLOTS][StepCfg<DT>::THREADS];
-    G gf[META_SLOTS][StepCfg<DT>::THREADS];
     E data[DATA_SLOTS][Q][StepCfg<DT>::THREADS];
+    // last, so that a launch without a per-node force field leaves it out of the dynamic
+    // shared memory (the space goes to the L1 cache, which serves the 4-byte gathers)
+    G gf[META_SLOTS][StepCfg<DT>::THREADS];
 };
 
 __device__ __forceinline__ void issue_hdr(int4* hdr, int64_t grp, int64_t n_groups, const int4* __restrict__ groups) {
@@ -297,7 +302,8 @@ static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     const int from = A == c->f[0] ? 0 : 1;
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
-    k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, sizeof(StepSmem<DT>), c->stream>>>(
+    const size_t smem = c->gfield ? sizeof(StepSmem<DT>) : offsetof(StepSmem<DT>, gf);
+    k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, smem, c->stream>>>(
         (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
         seed_in, seed_out);
     return cudaGetLastError();
