@@ -22,6 +22,7 @@
 //             results into the other copy.
 // Solid nodes issue no copies and no stores.
 #include <algorithm>
+#include <cmath>
 #include <cstddef>
 
 #include "lbm_collide.cuh"
@@ -30,15 +31,24 @@
 
 namespace lbm {
 
-// Threads per CTA (one per non-solid node of a work group) and resident CTAs per SM the
-// kernel is compiled for. The 4-byte-or-smaller formats: 4 CTAs of 256 threads (about 46 KB
-// of shared memory each; 8 CTAs of 128 threads, the same warps with half the work per
-// group, run 25 % slower, and 2 CTAs of 512 threads 1-2 % slower). FP64: 2 CTAs of 256 threads (about 90 KB each, up to 128
-// registers); 3 CTAs of 192 threads would give 18 warps per SM instead of 16, but cap the
-// registers at 96, and the double-float collision then spills and runs 20 % slower.
+// Threads per CTA (one per non-solid node of a work group), resident CTAs per SM and the
+// tile limit of a work group, per storage format. The CTA count also sets the shared
+// memory carveout, and what is left of the SM's 256 KB serves as L1 for the gathers:
+//   FP16: 4 CTAs of 256 threads (44 KB of shared memory each, 60 KB of L1).
+//   FP32: 3 CTAs of 256 threads (92 KB of L1; 6 % faster than 4 CTAs with 60 KB).
+//   FP64: 2 CTAs of 256 threads (90 KB each, up to 128 registers); 3 CTAs of 192 threads
+//         cap the registers at 96, and the double-float collision then spills (-20 %).
+// Measured and not kept: 8 CTAs of 128 threads (-25 %), 2 of 512 (-1 to -2 %), groups of
+// 16 tiles for the 4-byte formats (their larger neighbour staging pushes 4 CTAs past the
+// 196 KB carveout, leaving 28 KB of L1: -25 %).
 template <int DT> struct StepCfg {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 4;
+    static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
+};
+template <> struct StepCfg<LBM_F32> {
+    static constexpr int THREADS = 256;
+    static constexpr int CTAS = 3;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
 };
 template <> struct StepCfg<LBM_F64> {
@@ -217,9 +227,6 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     }
 }
 
-// Resident CTAs per SM the kernel is compiled for: shared memory allows 4 CTAs of the
-// 4-byte formats (about 46 KB each) and 2 of FP64 (about 88 KB each); registers match.
-
 template <int DT, bool VAR, int MODE, bool GEN>
 __global__ void __launch_bounds__(StepCfg<DT>::THREADS, StepCfg<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
@@ -278,32 +285,53 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     cp_async_wait<0>();
 }
 
+// Shared memory of a launch: the whole StepSmem with a per-node force field, without its
+// force staging (the last member) otherwise.
+template <int DT>
+static size_t step_smem(bool with_gf) {
+    return with_gf ? sizeof(StepSmem<DT>) : offsetof(StepSmem<DT>, gf);
+}
+
+// Persistent grid of StepCfg::CTAS CTAs per SM. Shared memory and L1 share one array per
+// SM; the kernel's preferred carveout is set to what those CTAs need (with the force
+// staging, the larger case) so that the rest stays L1, which serves the 4-byte gathers
+// (cp.async.ca). Left to itself the driver picks the carveout for the highest occupancy:
+// a light kernel (the calibration kinds) would fit a fifth CTA and keep 28 KB of L1
+// instead of 60 KB, and run 25 % slower.
 template <int DT, bool VAR, int MODE, bool GEN>
-static int step_grid(int64_t n_groups) {
-    static int per_sm = -1, n_sm = 0;
-    if (per_sm < 0) {
-        int dev = 0;
+static int step_grid(int64_t n_groups, bool with_gf) {
+    static int per_sm[2] = {-1, -1}, n_sm = 0;
+    int& ps = per_sm[with_gf ? 1 : 0];
+    if (ps < 0) {
+        int dev = 0, smem_sm = 0, reserved = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
         cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_step<DT, VAR, MODE, GEN>, StepCfg<DT>::THREADS,
-                                                      sizeof(StepSmem<DT>));
-        if (per_sm < 1) per_sm = 1;
+        if (smem_sm > 0) {
+            const double need = (double)StepCfg<DT>::CTAS * (double)(sizeof(StepSmem<DT>) + (size_t)reserved);
+            const int pct = std::min(100, std::max(1, (int)std::ceil(100.0 * need / smem_sm)));
+            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+        }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN>, StepCfg<DT>::THREADS,
+                                                      step_smem<DT>(with_gf));
+        ps = std::max(1, std::min(ps, StepCfg<DT>::CTAS));
     }
-    return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)per_sm * n_sm));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)ps * n_sm));
 }
 
 template <int DT, bool VAR, int MODE, bool GEN>
 static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
-    const int grid = step_grid<DT, VAR, MODE, GEN>(c->n_groups);
+    const bool with_gf = c->gfield != nullptr;
+    const int grid = step_grid<DT, VAR, MODE, GEN>(c->n_groups, with_gf);
     // the copy read decides which counter is read and which is advanced
     const int from = A == c->f[0] ? 0 : 1;
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
-    const size_t smem = c->gfield ? sizeof(StepSmem<DT>) : offsetof(StepSmem<DT>, gf);
-    k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, smem, c->stream>>>(
+    k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
         (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
         seed_in, seed_out);
     return cudaGetLastError();
@@ -337,13 +365,13 @@ template <bool GEN>
 static void prepare_model(lbm_ctx* c) {
     switch (c->dtype) {
         case LBM_F64:
-            if (c->native64) step_grid<LBM_F64, true, STEP_FULL, GEN>(1);
-            else step_grid<LBM_F64, false, STEP_FULL, GEN>(1);
+            if (c->native64) step_grid<LBM_F64, true, STEP_FULL, GEN>(1, c->gfield != nullptr);
+            else step_grid<LBM_F64, false, STEP_FULL, GEN>(1, c->gfield != nullptr);
             break;
-        case LBM_F32: step_grid<LBM_F32, false, STEP_FULL, GEN>(1); break;
+        case LBM_F32: step_grid<LBM_F32, false, STEP_FULL, GEN>(1, c->gfield != nullptr); break;
         default:
-            if (c->sr) step_grid<LBM_F16S, true, STEP_FULL, GEN>(1);
-            else step_grid<LBM_F16S, false, STEP_FULL, GEN>(1);
+            if (c->sr) step_grid<LBM_F16S, true, STEP_FULL, GEN>(1, c->gfield != nullptr);
+            else step_grid<LBM_F16S, false, STEP_FULL, GEN>(1, c->gfield != nullptr);
     }
 }
 
