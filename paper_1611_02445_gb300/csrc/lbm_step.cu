@@ -122,16 +122,15 @@ __device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const in
     }
 }
 
-// Issue the 19 gathers of this thread's node. Returns, for F16S, the mask of directions
-// whose half is the upper half of the staged word.
+// Issue the 19 gathers of this thread's node (for F16S the aligned 32-bit word that holds
+// the wanted half).
 template <int DT, int MODE>
-__device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, int dslot, const int4 h,
-                                                 const typename Store<DT>::T* __restrict__ A) {
+__device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int dslot, const int4 h,
+                                             const typename Store<DT>::T* __restrict__ A) {
     using T = typename Store<DT>::T;
     const int t = threadIdx.x;
     const uint32_t w = sm.word[mslot][t];
-    uint32_t odd = 0;
-    if (((w >> WORD_TYPE_SHIFT) & 3u) == LBM_SOLID) return 0;
+    if (((w >> WORD_TYPE_SHIFT) & 3u) == LBM_SOLID) return;
     const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
     const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
@@ -153,15 +152,26 @@ __device__ __forceinline__ uint32_t issue_gather(StepSmem<DT>& sm, int mslot, in
         } else if (DT == LBM_F32) {
             cp_async4(&sm.data[dslot][i][t], A + src);
         } else {
-            odd |= (uint32_t)(src & 1) << i;
             cp_async4(&sm.data[dslot][i][t], reinterpret_cast<const char*>(A) + (src & ~(int64_t)1) * sizeof(T));
         }
     }
-    return odd;
+}
+
+// Directions with c_x != 0 (1, 3, 7-14).
+constexpr uint32_t CX_DIRS = (1u << 1) | (1u << 3) | (0xffu << 7);
+
+// F16S: which directions' values are the upper half of their staged 32-bit word. Data
+// blocks start at even element indices, so the half is the upper one when the source
+// slot is odd: a pulled source has slot parity (x - c_x) & 1, a bounced (or read/write)
+// source is the node's own slot, parity x & 1.
+template <int MODE>
+__device__ __forceinline__ uint32_t upper_halves(int s, uint32_t w) {
+    const uint32_t own = (s & 1) ? 0x7ffffu : 0u;
+    return MODE == STEP_RW ? own : own ^ (CX_DIRS & ~w);
 }
 
 template <int DT, bool VAR, int MODE, bool GEN>
-__device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, uint32_t odd,
+__device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h,
                                               typename Store<DT>::T* __restrict__ B, const StepParams& p,
                                               bool has_gf, uint32_t key) {
     using R = typename Store<DT>::R;
@@ -172,12 +182,13 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     if (type == LBM_SOLID) return;
     const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     R v[Q];
+    const uint32_t odd = DT == LBM_F16S ? upper_halves<MODE>(s, w) : 0u;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         T e;
         if (DT == LBM_F16S) {
             const uint32_t word = (uint32_t)sm.data[dslot][i][t];
-            const unsigned short hbits = (unsigned short)(((odd >> i) & 1) ? (word >> 16) : (word & 0xffffu));
+            const unsigned short hbits = (unsigned short)(word >> (((odd >> i) & 1u) << 4));
             e = *reinterpret_cast<const T*>(&hbits);
         } else {
             const typename Staged<DT>::E raw = sm.data[dslot][i][t];
@@ -262,7 +273,7 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    uint32_t odd_cur = issue_gather<DT, MODE>(sm, 0, 0, sm.hdr[0], A);
+    issue_gather<DT, MODE>(sm, 0, 0, sm.hdr[0], A);
     cp_async_commit();
     int it = 0;
     for (int64_t g = g0; g < n_groups; g += G, it++) {
@@ -273,14 +284,11 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         cp_async_commit();
         if (g + 2 * G < n_groups) issue_meta<DT>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], nbr, fword, gfield_c);
         cp_async_commit();
-        uint32_t odd_next = 0;
-        if (g + G < n_groups)
-            odd_next = issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
+        if (g + G < n_groups) issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
         cp_async_commit();
         // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
         cp_async_wait<3>();
-        compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], odd_cur, B, p, has_gf, key);
-        odd_cur = odd_next;
+        compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], B, p, has_gf, key);
     }
     cp_async_wait<0>();
 }
