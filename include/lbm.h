@@ -92,6 +92,8 @@ enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
  *               padded with solid nodes (Sec. 3.1).
  *   stream      cudaStream_t to queue work on (NULL = legacy default stream).
  *   out         receives the new context, or NULL on failure.
+ * Limits: at most 2^31 / 64 kept tiles (2^31 node slots; per-node indices are 32-bit),
+ * else LBM_EUNSUPPORTED; device memory for two population copies (LBM_ENOMEM).
  * The populations are not initialised: call lbm_init_equilibrium or lbm_set_f. */
 lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, int nz, int tile,
                       lbm_dtype dtype, unsigned periodic, void* stream, lbm_ctx** out);

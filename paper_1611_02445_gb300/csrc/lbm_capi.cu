@@ -289,6 +289,11 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
         fail(c, LBM_EINTERNAL, "tile count out of range");
         return bail(LBM_EINTERNAL);
     }
+    if (count > (int64_t)(0x7fffffff / lbm::SLOTS)) {
+        // per-node slot indices (tile * 64 + slot) and work-group node offsets are 32-bit
+        fail(c, LBM_EUNSUPPORTED, "more than 2^31 / 64 kept tiles (2^31 node slots) are not supported");
+        return bail(LBM_EUNSUPPORTED);
+    }
     c->n_tiles = count;
     const size_t copy_bytes = (size_t)count * lbm::Q * lbm::SLOTS * lbm::dtype_size(dtype);
     c->n_partials = lbm::reduce_blocks(count);
