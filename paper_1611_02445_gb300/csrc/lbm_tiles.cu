@@ -435,15 +435,9 @@ __global__ void k_macro(const typename Store<DT>::T* __restrict__ f, const uint6
         const int y = TILE * (int)((t / (uint32_t)Tx) % (uint32_t)Ty) + ((s >> 2) & 3);
         const int z = TILE * (int)(t / ((uint32_t)Tx * (uint32_t)Ty)) + (s >> 4);
         const int64_t node = x + (int64_t)nx * (y + (int64_t)ny * z);
-        double r = 0.0, jx = 0.0, jy = 0.0, jz = 0.0;
-#pragma unroll
-        for (int i = 0; i < Q; i++) {
-            const double v = to_f64<DT>(f[(k * Q + i) * SLOTS + s], i);
-            r += v;
-            jx += cx(i) * v;
-            jy += cy(i) * v;
-            jz += cz(i) * v;
-        }
+        double m[4];
+        node_moments<DT>(f, k, s, m);
+        const double r = m[0], jx = m[1], jy = m[2], jz = m[3];
         const double Fx = gfield ? gfield_at<DT>(gfield, idx) : p.g[0];
         rho[node] = (O)r;
         if (p.eq == LBM_EQ_INCOMPR) {
