@@ -610,9 +610,9 @@ FP64_FLOPS_PER_NODE = 331
 # DRAM bytes (read + write) per non-solid node of one step launch, from ncu on the 128^3
 # pack (scaled to a launch by the number of non-solid nodes); None where not captured for
 # the current kernel.
-TRAFFIC_PER_NODE = {"f64": (231.976960e6 + 106.915328e6) / 732512,
-                    "f32": (131.340032e6 + 48.508672e6) / 732512,
-                    "f16s": (76.772864e6 + 23.994624e6) / 732512}
+TRAFFIC_PER_NODE = {"f64": (231.857920e6 + 106.886144e6) / 732512,
+                    "f32": (131.165952e6 + 48.392960e6) / 732512,
+                    "f16s": (76.658432e6 + 24.017152e6) / 732512}
 
 if __name__ == "__main__":
     main()
