@@ -103,7 +103,7 @@ void free_all(lbm_ctx* c) {
     drop_graphs(c);
     void* bufs[] = {c->tile_map, c->non_empty, c->nbr,    c->smask,  c->tflags, c->ntype,    c->nword,
                     c->groups,   c->fword,     c->fidx,   c->gfield, c->gfield_c, c->f[0], c->f[1],
-                    c->partials, c->d_out, c->seed};
+                    c->partials, c->d_out, c->seed, c->gfill_rng, c->gfill};
     for (void* b : bufs)
         if (b) cudaFree(b);
     c->tile_map = nullptr;
@@ -116,6 +116,8 @@ void free_all(lbm_ctx* c) {
     c->groups = nullptr;
     c->fword = nullptr;
     c->fidx = nullptr;
+    c->gfill_rng = nullptr;
+    c->gfill = nullptr;
     c->gfield_c = nullptr;
     c->f[0] = c->f[1] = nullptr;
     c->gfield = nullptr;
@@ -339,6 +341,11 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
         }
         std::vector<int4> groups;
         std::vector<uint32_t> fw, fi;
+        // fill lists: the solid and padding slots of every 32-byte sector that also holds a
+        // non-solid slot, per group (one list serves all 19 data blocks of a tile)
+        std::vector<int2> fill_rng;
+        std::vector<uint32_t> fill;
+        const int sector = lbm::fill_sector_slots(dtype);
         const int max_nodes = dtype == LBM_F64 ? lbm::GROUP_MAX_NODES_F64 : lbm::GROUP_MAX_NODES;
         const int max_tiles = dtype == LBM_F64 ? lbm::GROUP_MAX_TILES_F64 : lbm::GROUP_MAX_TILES_4B;
         fw.reserve((size_t)nonsolid);
@@ -350,6 +357,7 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
             g.y = 0;
             g.z = (int)fw.size();
             g.w = 0;
+            const size_t fill0 = fill.size();
             while (k < count && g.y < max_tiles) {
                 int cnt = 0;
                 for (int sl = 0; sl < lbm::SLOTS; sl++) cnt += (words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) != 0;
@@ -360,17 +368,35 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
                     fw.push_back(w | ((uint32_t)g.y << lbm::WORD_LT_SHIFT) | ((uint32_t)sl << lbm::WORD_SLOT_SHIFT));
                     fi.push_back((uint32_t)(k * lbm::SLOTS + sl));
                 }
+                for (int sb = 0; sector > 0 && sb < lbm::SLOTS; sb += sector) {
+                    bool any = false;
+                    for (int sl = sb; sl < sb + sector; sl++) any |= (words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) != 0;
+                    if (!any) continue;
+                    for (int sl = sb; sl < sb + sector; sl++)
+                        if ((words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) == 0)
+                            fill.push_back((uint32_t)(g.y * lbm::SLOTS + sl));
+                }
                 g.w += cnt;
                 g.y++;
                 k++;
             }
             groups.push_back(g);
+            fill_rng.push_back(make_int2((int)fill0, (int)(fill.size() - fill0)));
         }
         if ((int64_t)fw.size() != c->n_nonsolid) {
             fail(c, LBM_EINTERNAL, "non-solid node count mismatch while building work groups");
             return bail(LBM_EINTERNAL);
         }
         c->n_groups = (int64_t)groups.size();
+        c->n_fill = (int64_t)fill.size();
+        LBM_CREATE_CUDA(dev_alloc(&c->gfill_rng, fill_rng.size()));
+        LBM_CREATE_CUDA(dev_alloc(&c->gfill, fill.size()));
+        if (!fill_rng.empty())
+            LBM_CREATE_CUDA(cudaMemcpyAsync(c->gfill_rng, fill_rng.data(), fill_rng.size() * sizeof(int2),
+                                            cudaMemcpyHostToDevice, c->stream));
+        if (!fill.empty())
+            LBM_CREATE_CUDA(cudaMemcpyAsync(c->gfill, fill.data(), fill.size() * sizeof(uint32_t),
+                                            cudaMemcpyHostToDevice, c->stream));
         LBM_CREATE_CUDA(dev_alloc(&c->groups, groups.size()));
         LBM_CREATE_CUDA(dev_alloc(&c->fword, fw.size()));
         LBM_CREATE_CUDA(dev_alloc(&c->fidx, fi.size()));

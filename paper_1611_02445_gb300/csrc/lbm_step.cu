@@ -20,7 +20,9 @@
 //             or Zou-He completion then collision), the collision (LBGK + Guo, Eq. 2, 3,
 //             7; or the incompressible / MRT models) and coalesced stores of all 19
 //             results into the other copy.
-// Solid nodes issue no copies and no stores.
+// Solid nodes issue no copies. With FP32 storage a solid slot that shares a 32-byte sector
+// with a non-solid one gets its NaN stored again (the group's fill list), so that every
+// sector the step writes is written whole.
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
@@ -41,20 +43,24 @@ namespace lbm {
 // Measured and not kept: 8 CTAs of 128 threads (-25 %), 2 of 512 (-1 to -2 %), groups of
 // 16 tiles for the 4-byte formats (their larger neighbour staging pushes 4 CTAs past the
 // 196 KB carveout, leaving 28 KB of L1: -25 %).
+// FILL: the format stores NaN into its groups' fill slots (full-sector writes).
 template <int DT> struct StepCfg {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 4;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
+    static constexpr bool FILL = fill_sector_slots(DT) > 0;
 };
 template <> struct StepCfg<LBM_F32> {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 3;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
+    static constexpr bool FILL = fill_sector_slots(LBM_F32) > 0;
 };
 template <> struct StepCfg<LBM_F64> {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 2;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_F64;
+    static constexpr bool FILL = fill_sector_slots(LBM_F64) > 0;
 };
 static_assert(StepCfg<LBM_F32>::THREADS == GROUP_MAX_NODES && StepCfg<LBM_F64>::THREADS == GROUP_MAX_NODES_F64,
               "work groups and CTAs must agree");
@@ -89,23 +95,34 @@ struct StepSmem {
     using E = typename Staged<DT>::E;
     using G = typename Store<DT>::R;
     int4 hdr[HDR_SLOTS];                                   // {t0, tiles, f0, nodes}
+    int2 frng[HDR_SLOTS];                                  // {first fill entry, fill entries}
     int32_t nbr[META_SLOTS][StepCfg<DT>::MAX_TILES][NBR_STRIDE];
     uint32_t word[META_SLOTS][StepCfg<DT>::THREADS];
+    uint32_t fill[META_SLOTS][StepCfg<DT>::FILL ? StepCfg<DT>::THREADS : 1];   // fill entry THREADS - 1 - t
     E data[DATA_SLOTS][Q][StepCfg<DT>::THREADS];
     // last, so that a launch without a per-node force field leaves it out of the dynamic
     // shared memory (the space goes to the L1 cache, which serves the 4-byte gathers)
     G gf[META_SLOTS][StepCfg<DT>::THREADS];
 };
 
-__device__ __forceinline__ void issue_hdr(int4* hdr, int64_t grp, int64_t n_groups, const int4* __restrict__ groups) {
+template <bool FILL>
+__device__ __forceinline__ void issue_hdr(int4* hdr, int2* frng, int64_t grp, int64_t n_groups,
+                                          const int4* __restrict__ groups, const int2* __restrict__ gfill_rng) {
     if (threadIdx.x == 0 && grp < n_groups) cp_async16(hdr, groups + grp);
+    if (FILL && threadIdx.x == 32 && grp < n_groups) cp_async8(frng, gfill_rng + grp);
 }
 
-// Neighbour records of the group's tiles, and the words (and forces) of its nodes.
+// Neighbour records of the group's tiles, the words (and forces) of its nodes and the
+// first THREADS entries of its fill list.
 template <int DT>
-__device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const int4 h, const int32_t* __restrict__ nbr,
-                                           const uint32_t* __restrict__ fword, const void* gfield_c) {
+__device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const int4 h, const int2 fr,
+                                           const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
+                                           const void* gfield_c, const uint32_t* __restrict__ gfill) {
     const int t = threadIdx.x;
+    if constexpr (StepCfg<DT>::FILL) {
+        const int j0 = StepCfg<DT>::THREADS - 1 - t;
+        if (j0 < fr.y) cp_async4(&sm.fill[mslot][t], gfill + fr.x + j0);
+    }
     if (t < h.y * (NBR_STRIDE / 4)) {
         const int lt = t / (NBR_STRIDE / 4), c = t % (NBR_STRIDE / 4);
         cp_async16(&sm.nbr[mslot][lt][4 * c], nbr + (int64_t)(h.x + lt) * NBR_STRIDE + 4 * c);
@@ -238,12 +255,32 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     }
 }
 
+// NaN into the group's fill slots (solid or padding slots that share a 32-byte sector with
+// a non-solid slot), in all 19 data blocks. Together with the nodes' own stores every
+// sector the step writes is then written whole; a partly written sector would cost DRAM a
+// read of the sector to merge it. The slots hold NaN already, so nothing changes. Entry j
+// goes to thread THREADS - 1 - j, where the idle threads of a short group are; e0 is this
+// thread's first entry, staged in shared memory with the group's other metadata.
+template <int DT>
+__device__ __forceinline__ void fill_solid(typename Store<DT>::T* __restrict__ B, int t0, uint32_t e0,
+                                           const uint32_t* __restrict__ list, int nf) {
+    using T = typename Store<DT>::T;
+    const T nan = nan_value<DT>();
+    int j = StepCfg<DT>::THREADS - 1 - (int)threadIdx.x;
+    for (uint32_t e = e0; j < nf; j += StepCfg<DT>::THREADS) {
+        if (j >= StepCfg<DT>::THREADS) e = __ldg(list + j);
+        T* q = B + (int64_t)(t0 + (int)(e >> 6)) * (Q * SLOTS) + (e & 63u);
+#pragma unroll
+        for (int i = 0; i < Q; i++) q[i * SLOTS] = nan;
+    }
+}
+
 template <int DT, bool VAR, int MODE, bool GEN>
 __global__ void __launch_bounds__(StepCfg<DT>::THREADS, StepCfg<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
-       const void* __restrict__ gfield_c, int64_t n_groups, StepParams p, const uint32_t* __restrict__ seed_in,
-       uint32_t* __restrict__ seed_out) {
+       const void* __restrict__ gfield_c, const int2* __restrict__ gfill_rng, const uint32_t* __restrict__ gfill,
+       int64_t n_groups, StepParams p, const uint32_t* __restrict__ seed_in, uint32_t* __restrict__ seed_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<DT>& sm = *reinterpret_cast<StepSmem<DT>*>(smem_raw);
     const int64_t G = gridDim.x;
@@ -259,17 +296,17 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     if (g0 >= n_groups) return;
     const bool has_gf = gfield_c != nullptr;
     // prologue: headers of groups 0..2, meta of groups 0..1, gathers of group 0
-    issue_hdr(&sm.hdr[0], g0, n_groups, groups);
+    issue_hdr<StepCfg<DT>::FILL>(&sm.hdr[0], &sm.frng[0], g0, n_groups, groups, gfill_rng);
     cp_async_commit();
-    issue_hdr(&sm.hdr[1], g0 + G, n_groups, groups);
+    issue_hdr<StepCfg<DT>::FILL>(&sm.hdr[1], &sm.frng[1], g0 + G, n_groups, groups, gfill_rng);
     cp_async_commit();
-    issue_hdr(&sm.hdr[2], g0 + 2 * G, n_groups, groups);
+    issue_hdr<StepCfg<DT>::FILL>(&sm.hdr[2], &sm.frng[2], g0 + 2 * G, n_groups, groups, gfill_rng);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    issue_meta<DT>(sm, 0, sm.hdr[0], nbr, fword, gfield_c);
+    issue_meta<DT>(sm, 0, sm.hdr[0], sm.frng[0], nbr, fword, gfield_c, gfill);
     cp_async_commit();
-    if (g0 + G < n_groups) issue_meta<DT>(sm, 1, sm.hdr[1], nbr, fword, gfield_c);
+    if (g0 + G < n_groups) issue_meta<DT>(sm, 1, sm.hdr[1], sm.frng[1], nbr, fword, gfield_c, gfill);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
@@ -280,15 +317,22 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         // pending: header(g + 2G) [done], meta(g + G), gather(g)
         cp_async_wait<1>();
         __syncthreads();   // header(g + 2G), meta(g + G) visible; iteration it - 1 finished
-        issue_hdr(&sm.hdr[(it + 3) & 3], g + 3 * G, n_groups, groups);
+        issue_hdr<StepCfg<DT>::FILL>(&sm.hdr[(it + 3) & 3], &sm.frng[(it + 3) & 3], g + 3 * G, n_groups, groups,
+                                     gfill_rng);
         cp_async_commit();
-        if (g + 2 * G < n_groups) issue_meta<DT>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], nbr, fword, gfield_c);
+        if (g + 2 * G < n_groups)
+            issue_meta<DT>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], sm.frng[(it + 2) & 3], nbr, fword,
+                           gfield_c, gfill);
         cp_async_commit();
         if (g + G < n_groups) issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
         cp_async_commit();
         // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
         cp_async_wait<3>();
         compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], B, p, has_gf, key);
+        if constexpr (StepCfg<DT>::FILL) {
+            const int2 fr = sm.frng[it & 3];
+            fill_solid<DT>(B, sm.hdr[it & 3].x, sm.fill[it % META_SLOTS][threadIdx.x], gfill + fr.x, fr.y);
+        }
     }
     cp_async_wait<0>();
 }
@@ -340,8 +384,8 @@ static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
     k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
-        (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
-        seed_in, seed_out);
+        (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->gfill_rng, c->gfill,
+        c->n_groups, c->p, seed_in, seed_out);
     return cudaGetLastError();
 }
 
