@@ -531,13 +531,11 @@ def main():
                 "peak_source": "FP64 FMA pipe: 152 SMs x 2 DFMA/clk x 2 FLOP x 2.07 GHz (probe measured 1.20)",
                 "fp64_flops_per_node_update": flops_per_node,
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak}}
-    roof["traffic"] = TRAFFIC_PER_NODE.get(args.dtype) if args.kernel == "full" and args.model == "bgk" else None
-    if roof["traffic"] is not None and args.size == 256:
-        roof["traffic"] = roof["traffic"] * n_nonsolid
-        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch on the 128^3 "
-                                  "pack, per non-solid node, times this launch's non-solid nodes")
-    else:
-        roof["traffic"] = None
+    full_size = args.kernel == "full" and args.model == "bgk" and args.size == 256
+    roof["traffic"] = TRAFFIC_PER_LAUNCH_256.get(args.dtype) if full_size else None
+    if roof["traffic"] is not None:
+        roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this launch (porous 256^3 "
+                                  "pack), mean of two captured launches")
 
     line = {"metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -607,12 +605,12 @@ MODEL_NAME = {"bgk": "LBGK, quasi-compressible equilibrium (Eq. 3)",
 # of 2 * dfma + dadd + dmul over one launch on the 128^3 pack, divided by its 732 512 nodes.
 FP64_FLOPS_PER_NODE = 331
 
-# DRAM bytes (read + write) per non-solid node of one step launch, from ncu on the 128^3
-# pack (scaled to a launch by the number of non-solid nodes); None where not captured for
-# the current kernel.
-TRAFFIC_PER_NODE = {"f64": (231.857920e6 + 106.886144e6) / 732512,
-                    "f32": (131.165952e6 + 48.392960e6) / 732512,
-                    "f16s": (76.658432e6 + 24.017152e6) / 732512}
+# DRAM bytes (read + write) of one step launch on the porous 256^3 pack, from a one-pass
+# ncu capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean of
+# two launches after three warm-up steps); absent where not captured for the current kernel.
+TRAFFIC_PER_LAUNCH_256 = {"f64": 1988451072 + 1108048896,
+                          "f32": 855424256 + 578127104,
+                          "f16s": 822345472 + 329302144}
 
 if __name__ == "__main__":
     main()

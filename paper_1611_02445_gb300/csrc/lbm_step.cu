@@ -114,12 +114,12 @@ __device__ __forceinline__ void issue_hdr(int4* hdr, int2* frng, int64_t grp, in
 
 // Neighbour records of the group's tiles, the words (and forces) of its nodes and the
 // first THREADS entries of its fill list.
-template <int DT>
+template <int DT, bool FL>
 __device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const int4 h, const int2 fr,
                                            const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
                                            const void* gfield_c, const uint32_t* __restrict__ gfill) {
     const int t = threadIdx.x;
-    if constexpr (StepCfg<DT>::FILL) {
+    if constexpr (FL) {
         const int j0 = StepCfg<DT>::THREADS - 1 - t;
         if (j0 < fr.y) cp_async4(&sm.fill[mslot][t], gfill + fr.x + j0);
     }
@@ -275,7 +275,8 @@ __device__ __forceinline__ void fill_solid(typename Store<DT>::T* __restrict__ B
     }
 }
 
-template <int DT, bool VAR, int MODE, bool GEN>
+// FL: the geometry has fill slots (FP32 storage only; see fill_solid).
+template <int DT, bool VAR, int MODE, bool GEN, bool FL>
 __global__ void __launch_bounds__(StepCfg<DT>::THREADS, StepCfg<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
@@ -296,17 +297,17 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     if (g0 >= n_groups) return;
     const bool has_gf = gfield_c != nullptr;
     // prologue: headers of groups 0..2, meta of groups 0..1, gathers of group 0
-    issue_hdr<StepCfg<DT>::FILL>(&sm.hdr[0], &sm.frng[0], g0, n_groups, groups, gfill_rng);
+    issue_hdr<FL>(&sm.hdr[0], &sm.frng[0], g0, n_groups, groups, gfill_rng);
     cp_async_commit();
-    issue_hdr<StepCfg<DT>::FILL>(&sm.hdr[1], &sm.frng[1], g0 + G, n_groups, groups, gfill_rng);
+    issue_hdr<FL>(&sm.hdr[1], &sm.frng[1], g0 + G, n_groups, groups, gfill_rng);
     cp_async_commit();
-    issue_hdr<StepCfg<DT>::FILL>(&sm.hdr[2], &sm.frng[2], g0 + 2 * G, n_groups, groups, gfill_rng);
+    issue_hdr<FL>(&sm.hdr[2], &sm.frng[2], g0 + 2 * G, n_groups, groups, gfill_rng);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    issue_meta<DT>(sm, 0, sm.hdr[0], sm.frng[0], nbr, fword, gfield_c, gfill);
+    issue_meta<DT, FL>(sm, 0, sm.hdr[0], sm.frng[0], nbr, fword, gfield_c, gfill);
     cp_async_commit();
-    if (g0 + G < n_groups) issue_meta<DT>(sm, 1, sm.hdr[1], sm.frng[1], nbr, fword, gfield_c, gfill);
+    if (g0 + G < n_groups) issue_meta<DT, FL>(sm, 1, sm.hdr[1], sm.frng[1], nbr, fword, gfield_c, gfill);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
@@ -317,11 +318,11 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         // pending: header(g + 2G) [done], meta(g + G), gather(g)
         cp_async_wait<1>();
         __syncthreads();   // header(g + 2G), meta(g + G) visible; iteration it - 1 finished
-        issue_hdr<StepCfg<DT>::FILL>(&sm.hdr[(it + 3) & 3], &sm.frng[(it + 3) & 3], g + 3 * G, n_groups, groups,
+        issue_hdr<FL>(&sm.hdr[(it + 3) & 3], &sm.frng[(it + 3) & 3], g + 3 * G, n_groups, groups,
                                      gfill_rng);
         cp_async_commit();
         if (g + 2 * G < n_groups)
-            issue_meta<DT>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], sm.frng[(it + 2) & 3], nbr, fword,
+            issue_meta<DT, FL>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], sm.frng[(it + 2) & 3], nbr, fword,
                            gfield_c, gfill);
         cp_async_commit();
         if (g + G < n_groups) issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
@@ -329,7 +330,7 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
         cp_async_wait<3>();
         compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], B, p, has_gf, key);
-        if constexpr (StepCfg<DT>::FILL) {
+        if constexpr (FL) {
             const int2 fr = sm.frng[it & 3];
             fill_solid<DT>(B, sm.hdr[it & 3].x, sm.fill[it % META_SLOTS][threadIdx.x], gfill + fr.x, fr.y);
         }
@@ -350,7 +351,7 @@ static size_t step_smem(bool with_gf) {
 // (cp.async.ca). Left to itself the driver picks the carveout for the highest occupancy:
 // a light kernel (the calibration kinds) would fit a fifth CTA and keep 28 KB of L1
 // instead of 60 KB, and run 25 % slower.
-template <int DT, bool VAR, int MODE, bool GEN>
+template <int DT, bool VAR, int MODE, bool GEN, bool FL>
 static int step_grid(int64_t n_groups, bool with_gf) {
     static int per_sm[2] = {-1, -1}, n_sm = 0;
     int& ps = per_sm[with_gf ? 1 : 0];
@@ -360,33 +361,58 @@ static int step_grid(int64_t n_groups, bool with_gf) {
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
         if (smem_sm > 0) {
             const double need = (double)StepCfg<DT>::CTAS * (double)(sizeof(StepSmem<DT>) + (size_t)reserved);
             const int pct = std::min(100, std::max(1, (int)std::ceil(100.0 * need / smem_sm)));
-            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, FL>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
         }
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN>, StepCfg<DT>::THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN, FL>, StepCfg<DT>::THREADS,
                                                       step_smem<DT>(with_gf));
         ps = std::max(1, std::min(ps, StepCfg<DT>::CTAS));
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)ps * n_sm));
 }
 
-template <int DT, bool VAR, int MODE, bool GEN>
-static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
+template <int DT, bool VAR, int MODE, bool GEN, bool FL>
+static cudaError_t launch_step_fl(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
     const bool with_gf = c->gfield != nullptr;
-    const int grid = step_grid<DT, VAR, MODE, GEN>(c->n_groups, with_gf);
+    const int grid = step_grid<DT, VAR, MODE, GEN, FL>(c->n_groups, with_gf);
     // the copy read decides which counter is read and which is advanced
     const int from = A == c->f[0] ? 0 : 1;
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
-    k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
+    k_step<DT, VAR, MODE, GEN, FL><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
         (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->gfill_rng, c->gfill,
         c->n_groups, c->p, seed_in, seed_out);
     return cudaGetLastError();
+}
+
+// The fill stages run only where they pay: a geometry with fill slots (not dense) and an
+// LBGK collision. The MRT collision is bound by instruction issue like the FP64 and FP16
+// steps, and its FP32 step ran 6 % slower with them.
+static bool use_fill(const lbm_ctx* c) { return c->n_fill > 0 && c->p.coll == LBM_COLL_BGK; }
+
+template <int DT, bool VAR, int MODE, bool GEN>
+static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
+    if constexpr (StepCfg<DT>::FILL) {
+        if (use_fill(c)) return launch_step_fl<DT, VAR, MODE, GEN, true>(c, A, B);
+    }
+    return launch_step_fl<DT, VAR, MODE, GEN, false>(c, A, B);
+}
+
+template <int DT, bool VAR, bool GEN>
+static void prepare_dt(lbm_ctx* c) {
+    const bool with_gf = c->gfield != nullptr;
+    if constexpr (StepCfg<DT>::FILL) {
+        if (use_fill(c)) {
+            step_grid<DT, VAR, STEP_FULL, GEN, true>(1, with_gf);
+            return;
+        }
+    }
+    step_grid<DT, VAR, STEP_FULL, GEN, false>(1, with_gf);
 }
 
 template <int MODE, bool GEN>
@@ -417,13 +443,13 @@ template <bool GEN>
 static void prepare_model(lbm_ctx* c) {
     switch (c->dtype) {
         case LBM_F64:
-            if (c->native64) step_grid<LBM_F64, true, STEP_FULL, GEN>(1, c->gfield != nullptr);
-            else step_grid<LBM_F64, false, STEP_FULL, GEN>(1, c->gfield != nullptr);
+            if (c->native64) prepare_dt<LBM_F64, true, GEN>(c);
+            else prepare_dt<LBM_F64, false, GEN>(c);
             break;
-        case LBM_F32: step_grid<LBM_F32, false, STEP_FULL, GEN>(1, c->gfield != nullptr); break;
+        case LBM_F32: prepare_dt<LBM_F32, false, GEN>(c); break;
         default:
-            if (c->sr) step_grid<LBM_F16S, true, STEP_FULL, GEN>(1, c->gfield != nullptr);
-            else step_grid<LBM_F16S, false, STEP_FULL, GEN>(1, c->gfield != nullptr);
+            if (c->sr) prepare_dt<LBM_F16S, true, GEN>(c);
+            else prepare_dt<LBM_F16S, false, GEN>(c);
     }
 }
 

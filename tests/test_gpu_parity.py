@@ -230,6 +230,41 @@ def test_state_roundtrip_and_mismatch():
         assert e.value.status == 5
 
 
+@pytest.mark.parametrize("dtype", ["f32", "f64", "f16s"])
+def test_solid_slots_keep_their_nan(dtype):
+    """The step stores only into non-solid slots and, for FP32 storage, stores NaN again into
+    the solid and padding slots of every 32-byte sector it writes (full-sector writes): after
+    any number of steps, single launches or graph replays, the raw copy holds the canonical
+    NaN in every solid or padding slot of a kept tile and finite values everywhere else."""
+    nt = I.random_box(13, 10, 9, p_solid=0.45, seed=11)          # ragged: padding slots too
+    nz, ny, nx = nt.shape
+    Tx, Ty = (nx + 3) // 4, (ny + 3) // 4
+    elem, nan_bits, uint = {"f32": (np.float32, 0x7fc00000, np.uint32),
+                            "f64": (np.float64, 0x7ff8000000000000, np.uint64),
+                            "f16s": (np.float16, 0x7e00, np.uint16)}[dtype]
+    with lbm.Lattice(nt, dtype, 0) as L:                          # ragged axes cannot be periodic
+        L.set_params(0.7, g=(1e-5, 0.0, 0.0))
+        L.init_equilibrium()
+        _, ne = L.tiles()
+        s = np.arange(64)
+        t = ne.astype(np.int64)[:, None]
+        x = 4 * (t % Tx) + (s & 3)
+        y = 4 * ((t // Tx) % Ty) + ((s >> 2) & 3)
+        z = 4 * (t // (Tx * Ty)) + (s >> 4)
+        inside = (x < nx) & (y < ny) & (z < nz)
+        solid = ~inside
+        solid[inside] = nt[z[inside], y[inside], x[inside]] == 0
+        assert solid.any() and (~solid).any()
+        for steps in (1, 1, 2, 16, 17):
+            L.step(steps)
+            blob = L.save_state()
+            payload = np.frombuffer(blob[len(blob) - len(ne) * 19 * 64 * np.dtype(elem).itemsize:], dtype=elem)
+            f = payload.reshape(len(ne), 19, 64)
+            bits = f.view(uint).transpose(0, 2, 1)                 # [tile][slot][direction]
+            assert (bits[solid] == nan_bits).all()
+            assert np.isfinite(f.transpose(0, 2, 1)[~solid]).all()
+
+
 def test_argument_errors():
     nt = np.ones((8, 8, 8), np.uint8)
     with lbm.Lattice(nt, "f64", 0) as L:
