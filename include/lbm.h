@@ -83,7 +83,10 @@ enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
 /* Build a context for one geometry: validate the node types, build the tile map on
  * the GPU (Algorithm 1 of Sec. 3.1: tile_flag -> exclusive scan in z-y-x tile order ->
  * scatter of tileMap and nonEmptyTiles), build per-tile neighbour tables and node
- * masks, and allocate the two population copies A and B (Sec. 3.1, "two copies").
+ * masks, the work groups of the step kernel (for FP32 storage with the lists of solid
+ * slots that share a 32-byte sector with a non-solid slot: the step stores their NaN
+ * again, so that it writes whole sectors), and allocate the two population copies A
+ * and B (Sec. 3.1, "two copies").
  *   node_type   nx*ny*nz bytes, dense; host memory if on_device == 0, else a device
  *               pointer. Values other than 0..3 give LBM_EINVAL.
  *   tile        must be 4 (the paper's a = 4), else LBM_EUNSUPPORTED.

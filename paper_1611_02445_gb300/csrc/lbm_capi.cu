@@ -368,13 +368,13 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
                     fw.push_back(w | ((uint32_t)g.y << lbm::WORD_LT_SHIFT) | ((uint32_t)sl << lbm::WORD_SLOT_SHIFT));
                     fi.push_back((uint32_t)(k * lbm::SLOTS + sl));
                 }
+                const uint32_t* tw = &words[k * lbm::SLOTS];   // type 0: solid or padding
                 for (int sb = 0; sector > 0 && sb < lbm::SLOTS; sb += sector) {
                     bool any = false;
-                    for (int sl = sb; sl < sb + sector; sl++) any |= (words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) != 0;
+                    for (int sl = sb; sl < sb + sector; sl++) any |= (tw[sl] >> lbm::WORD_TYPE_SHIFT) != 0;
                     if (!any) continue;
                     for (int sl = sb; sl < sb + sector; sl++)
-                        if ((words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) == 0)
-                            fill.push_back((uint32_t)(g.y * lbm::SLOTS + sl));
+                        if ((tw[sl] >> lbm::WORD_TYPE_SHIFT) == 0) fill.push_back((uint32_t)(g.y * lbm::SLOTS + sl));
                 }
                 g.w += cnt;
                 g.y++;

@@ -43,7 +43,7 @@ namespace lbm {
 // Measured and not kept: 8 CTAs of 128 threads (-25 %), 2 of 512 (-1 to -2 %), groups of
 // 16 tiles for the 4-byte formats (their larger neighbour staging pushes 4 CTAs past the
 // 196 KB carveout, leaving 28 KB of L1: -25 %).
-// FILL: the format stores NaN into its groups' fill slots (full-sector writes).
+// FILL: the format has fill lists (full-sector writes, see fill_solid).
 template <int DT> struct StepCfg {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 4;
@@ -275,7 +275,8 @@ __device__ __forceinline__ void fill_solid(typename Store<DT>::T* __restrict__ B
     }
 }
 
-// FL: the geometry has fill slots (FP32 storage only; see fill_solid).
+// FL: this launch runs the fill stages (FP32 storage, an LBGK collision and a geometry with
+// fill slots; see use_fill).
 template <int DT, bool VAR, int MODE, bool GEN, bool FL>
 __global__ void __launch_bounds__(StepCfg<DT>::THREADS, StepCfg<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
@@ -318,12 +319,11 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         // pending: header(g + 2G) [done], meta(g + G), gather(g)
         cp_async_wait<1>();
         __syncthreads();   // header(g + 2G), meta(g + G) visible; iteration it - 1 finished
-        issue_hdr<FL>(&sm.hdr[(it + 3) & 3], &sm.frng[(it + 3) & 3], g + 3 * G, n_groups, groups,
-                                     gfill_rng);
+        issue_hdr<FL>(&sm.hdr[(it + 3) & 3], &sm.frng[(it + 3) & 3], g + 3 * G, n_groups, groups, gfill_rng);
         cp_async_commit();
         if (g + 2 * G < n_groups)
-            issue_meta<DT, FL>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], sm.frng[(it + 2) & 3], nbr, fword,
-                           gfield_c, gfill);
+            issue_meta<DT, FL>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], sm.frng[(it + 2) & 3], nbr,
+                               fword, gfield_c, gfill);
         cp_async_commit();
         if (g + G < n_groups) issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
         cp_async_commit();
