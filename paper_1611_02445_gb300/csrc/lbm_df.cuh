@@ -191,13 +191,23 @@ LBM_DF_HD int64_t fix_from_double(double d) {
     return (b >> 63) ? -r : r;
 }
 
-// Nearest double-float of x * 2^-58.
+// Double-float of x * 2^-58 (relative error below 2^-48), from three pieces that each
+// convert to FP32 exactly: x = t 2^41 + r1 2^18 + r0 with t = floor(x / 2^41) (|t| <= 2^22),
+// 0 <= r1 < 2^23 and 0 <= r0 < 2^18. A piece p becomes a float by the 2^23 magic-number
+// trick (the bit pattern of 2^23 + p, or 1.5 * 2^23 + t for the signed piece, minus that
+// constant), so no 64-bit integer conversion is executed: GB300 runs those on its 2-lane
+// FP64 pipe, where they took a third of the step's FP64 instructions.
+static_assert(FIX_SHIFT == 58, "df_from_fix splits x for 2^-58 fixed point");
 LBM_DF_HD dfl df_from_fix(int64_t x) {
-    const float h = (float)x;                         // round to nearest
-    const int64_t r = x - (int64_t)h;                 // exact: |h| < 2^63, h integral
-    const float l = (float)r;
-    const float sc = 1.0f / (float)(1ull << FIX_SHIFT);
-    return df_make(LBM_FMUL(h, sc), LBM_FMUL(l, sc));
+    const int32_t t = (int32_t)(x >> 41);
+    const uint32_t r1 = (uint32_t)(x >> 18) & 0x7fffffu;
+    const uint32_t r0 = (uint32_t)x & 0x3ffffu;
+    const float tf = LBM_FSUB(float_of(0x4B400000u + (uint32_t)t), 12582912.0f);
+    const float r1f = LBM_FSUB(float_of(0x4B000000u | r1), 8388608.0f);
+    const float r0f = LBM_FSUB(float_of(0x4B000000u | r0), 8388608.0f);
+    // t 2^-17 + r1 2^-40 exactly as a pair, then the last piece (below 2^-40) into its low part
+    const dfl s = two_sum(LBM_FMUL(tf, 0x1p-17f), LBM_FMUL(r1f, 0x1p-40f));
+    return df_make(s.h, LBM_FADD(s.l, LBM_FMUL(r0f, 0x1p-58f)));
 }
 
 }  // namespace lbm
