@@ -23,7 +23,9 @@ namespace lbm {
 // the rest weight 1/3, class 1 the axis weight 1/18, class 2 the diagonal weight 1/36.
 struct DFConst {
     double om1;          // 1 - omega
-    double ow_d[3];      // omega w in FP64, for the dominant term omega w rho
+    double ow_d[2];      // omega w0 2^-58, omega w1 2^-58 in FP64: the dominant term omega w rho
+                         // from the fixed-point density (w2 = w1 / 2 exactly, so omega w2 rho
+                         // is the class-1 product halved)
     dfl ow3[3];          // 3 omega w
     dfl om45, om15;      // 4.5 omega, 1.5 omega
     dfl b3, b9;          // 3 beta, 9 beta
@@ -45,7 +47,7 @@ LBM_DF_HD DFConst make_df_const(double omega, double beta, double Fy, double Fz)
     const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
     c.om1 = 1.0 - omega;
     for (int k = 0; k < 3; k++) {
-        c.ow_d[k] = omega * w[k];
+        if (k < 2) c.ow_d[k] = omega * w[k] * (1.0 / (double)(1ull << FIX_SHIFT));   // exact scaling
         c.ow3[k] = df_split_host(3.0 * omega * w[k]);
     }
     c.om45 = df_split_host(4.5 * omega);
@@ -112,17 +114,19 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K) {
     const dfl P = df_add(df_mul(K.om15, JJ), df_mul(K.b3, JF));
     const dfl winv1 = df_mul(K.w1, inv);
     const dfl winv2 = df_scale2(winv1, 0.5f);
-    // omega w rho dominates every Y_i, so it is formed in FP64 (one conversion and three
+    // omega w rho dominates every Y_i, so it is formed in FP64 (one conversion and two
     // multiplies per node): a double-float product with a rounded constant would leave a
-    // systematic relative bias of ~1e-15 that acts as a mass source
+    // systematic relative bias of ~1e-15 that acts as a mass source. The 2^-58 of the
+    // fixed point sits in the constants, and omega w2 rho = (omega w1 rho) / 2 exactly.
 #if defined(__CUDA_ARCH__)
-    const double rho_d = __dmul_rn(__ll2double_rn(rho), 1.0 / (double)(1ull << FIX_SHIFT));
+    const double rho_i = __ll2double_rn(rho);
 #else
-    const double rho_d = (double)rho * (1.0 / (double)(1ull << FIX_SHIFT));
+    const double rho_i = (double)rho;
 #endif
     dfl A[3];
-#pragma unroll
-    for (int k = 0; k < 3; k++) A[k] = df_from_double(K.ow_d[k] * rho_d);
+    A[0] = df_from_double(K.ow_d[0] * rho_i);
+    A[1] = df_from_double(K.ow_d[1] * rho_i);
+    A[2] = df_scale2(A[1], 0.5f);
     // rest population: Y0 = A0 - (w0 / rho) P
     const dfl Y0 = df_sub(A[0], df_mul(df_mul(K.w0, inv), P));
 #if defined(__CUDA_ARCH__)
