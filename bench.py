@@ -608,7 +608,7 @@ FP64_FLOPS_PER_NODE = 331
 # DRAM bytes (read + write) of one step launch on the porous 256^3 pack, from a one-pass
 # ncu capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean of
 # two launches after three warm-up steps); absent where not captured for the current kernel.
-TRAFFIC_PER_LAUNCH_256 = {"f64": 1983339392 + 1107858432,
+TRAFFIC_PER_LAUNCH_256 = {"f64": 1989303168 + 1107922432,
                           "f32": 855424256 + 578127104,
                           "f16s": 822345472 + 329302144}
 
