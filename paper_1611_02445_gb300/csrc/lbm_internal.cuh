@@ -17,10 +17,13 @@
 //                               per direction per tile (Sec. 3.2, Fig. 3), slot
 //                               s = x + 4 y + 16 z inside the tile (Eq. 11 order)
 //   gfield   [n_tiles][64]       optional per-node x force (double for F64, else float)
-//   groups   [n_groups] int4     work units of the step kernel: {first tile, tiles (<= 8),
-//                               first fluid node, fluid nodes (<= 256)}, consecutive tiles
+//   groups   [n_groups] int4     work units of the step kernel: {first tile, tiles (<= 16
+//                               for FP64 storage, <= 8 otherwise), first fluid node, fluid
+//                               nodes (<= 256)}, consecutive tiles
 //   fword    [n_fluid] uint32    the gather word of every non-solid node in group order,
-//                               plus bits 22-24 its tile within the group, 25-30 its slot
+//                               plus bit 19 set when the node lies on the moving lid face
+//                               (lbm_set_lid), bits 22-25 its tile within the group and
+//                               bits 26-31 its slot
 //   fidx     [n_fluid] uint32    k * 64 + s of every non-solid node in the same order
 //   gfill_rng[n_groups]  int2    {first entry, entries} of each work group's fill list
 //   gfill    [n_fill]    uint32  (tile within the group) * 64 + slot of every solid or padding
