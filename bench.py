@@ -166,7 +166,9 @@ def run_reference(args, nt, tau, g):
     value = n * args.steps / dt / 1e6
     sample = (f"z-slab 256x256x{nz_s} of the workload ({n} non-solid nodes; x, y periodic, z walls), "
               f"one dense FP64 oracle step per benchmark step, OpenMP over z on {threads} threads")
-    return {"metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": 0, "steps": args.steps,
+    # n_gpus is the N of the launch, as in the other arm; the oracle itself runs on the host
+    # cores (cpu_baseline.cores)
+    return {"metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
