@@ -589,7 +589,8 @@ def main():
         L.close()
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = oracle_baseline(nt, 10, 12.0, tau, g)
+        # about 15 s of oracle steps on the host cores (a bounded sample of the workload)
+        line["cpu_baseline"] = oracle_baseline(nt, 1000, 15.0, tau, g)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
