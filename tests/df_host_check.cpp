@@ -1,0 +1,114 @@
+// Host build of the FP64 step's hybrid arithmetic (the double-float helpers and the LBGK +
+// Guo collision that the CUDA kernel compiles from the same header), checked against
+// long-double evaluations. Prints one "name value" line per measured quantity; the pytest
+// wrapper (test_df_host.py) holds the bounds.
+#include <cmath>
+#include <cstdio>
+#include <random>
+
+#include "../paper_1611_02445_gb300/csrc/lbm_collide_df.cuh"
+
+using namespace lbm;
+typedef long double LD;
+
+// D3Q19 velocities in the library's numbering: 0 rest; 1 E 2 N 3 W 4 S 5 T 6 B;
+// 7 NE 8 NW 9 SW 10 SE; 11 ET 12 EB 13 WT 14 WB; 15 NT 16 NB 17 ST 18 SB.
+static const int CV[19][3] = {{0, 0, 0},  {1, 0, 0},   {0, 1, 0},  {-1, 0, 0}, {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                              {1, 1, 0},  {-1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {1, 0, 1},  {1, 0, -1}, {-1, 0, 1},
+                              {-1, 0, -1}, {0, 1, 1},  {0, 1, -1}, {0, -1, 1}, {0, -1, -1}};
+static LD weight(int i) { return i == 0 ? 1.0L / 3 : (i < 7 ? 1.0L / 18 : 1.0L / 36); }
+
+int main() {
+    std::mt19937_64 rng(20240611);
+    std::uniform_real_distribution<double> U(0.0, 1.0);
+
+    // fix_from_double: d 2^58 rounded to nearest, ties away from zero (exact reference)
+    long fix_bad = 0;
+    for (int n = 0; n < 2000000; n++) {
+        const double d = std::ldexp(1.0 + U(rng), -(int)(rng() % 24)) * ((rng() & 1) ? -1.0 : 1.0);
+        const LD ref = roundl((LD)d * 0x1p58L);
+        if ((LD)fix_from_double(d) != ref) fix_bad++;
+    }
+    std::printf("fix_mismatches %ld\n", fix_bad);
+
+    // df_from_fix: relative error of hi + lo against x 2^-58
+    double fix_rel = 0;
+    for (int n = 0; n < 2000000; n++) {
+        const int sh = (int)(rng() % 63);
+        int64_t x = (int64_t)(rng() >> (64 - sh - 1));
+        if (rng() & 1) x = -x;
+        if (x == 0) continue;
+        const dfl p = df_from_fix(x);
+        const LD ex = (LD)x * 0x1p-58L;
+        fix_rel = std::fmax(fix_rel, (double)(fabsl((LD)p.h + (LD)p.l - ex) / fabsl(ex)));
+    }
+    std::printf("df_from_fix_rel %.3e\n", fix_rel);
+
+    // df_from_double: relative error against d, 2^-40 <= |d| < 2
+    double dbl_rel = 0;
+    for (int n = 0; n < 2000000; n++) {
+        const double d = std::ldexp(1.0 + U(rng), -(int)(rng() % 40)) * ((rng() & 1) ? -1.0 : 1.0);
+        const dfl p = df_from_double(d);
+        dbl_rel = std::fmax(dbl_rel, (double)(fabsl((LD)p.h + (LD)p.l - (LD)d) / fabsl((LD)d)));
+    }
+    std::printf("df_from_double_rel %.3e\n", dbl_rel);
+
+    // df_to_double_pos: the nearest double to hi + lo (normalised positive pairs)
+    long round_bad = 0;
+    for (int n = 0; n < 2000000; n++) {
+        const float h = (float)std::ldexp(1.0 + U(rng), -(int)(rng() % 30));
+        const float l = (float)((U(rng) - 0.5) * std::ldexp((double)h, -24));
+        const dfl p = df_make(h, l);
+        const double ref = (double)((LD)h + (LD)l);   // exact sum, rounded once to nearest
+        if (df_to_double_pos(p) != ref) round_bad++;
+    }
+    std::printf("to_double_mismatches %ld\n", round_bad);
+
+    // collide_df against the LBGK + Guo update evaluated in long double
+    double coll_abs = 0, mass_rel = 0;
+    for (int n = 0; n < 200000; n++) {
+        const double tau = 0.51 + 1.5 * U(rng), omega = 1.0 / tau, beta = 1.0 - 0.5 / tau;
+        const double F[3] = {1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1)};
+        const DFConst K = make_df_const(omega, beta, F[1], F[2]);
+        double f[19];
+        const double u0[3] = {0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1)};
+        const double rho0 = 0.9 + 0.2 * U(rng);
+        for (int i = 0; i < 19; i++) {
+            const double cu = CV[i][0] * u0[0] + CV[i][1] * u0[1] + CV[i][2] * u0[2];
+            const double uu = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
+            const double fe = (double)weight(i) * rho0 * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * uu);
+            f[i] = fe * (1.0 + 0.02 * (2 * U(rng) - 1));
+        }
+        LD rho = 0, j[3] = {0, 0, 0};
+        for (int i = 0; i < 19; i++) {
+            rho += f[i];
+            for (int a = 0; a < 3; a++) j[a] += (LD)CV[i][a] * f[i];
+        }
+        LD u[3], uu = 0, uF = 0;
+        for (int a = 0; a < 3; a++) {
+            u[a] = (j[a] + 0.5L * F[a]) / rho;
+            uu += u[a] * u[a];
+            uF += u[a] * F[a];
+        }
+        LD ref[19], mass_in = 0, mass_ref = 0;
+        for (int i = 0; i < 19; i++) {
+            const LD cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+            const LD cF = CV[i][0] * (LD)F[0] + CV[i][1] * (LD)F[1] + CV[i][2] * (LD)F[2];
+            const LD feq = weight(i) * rho * (1 + 3 * cu + 4.5L * cu * cu - 1.5L * uu);
+            const LD S = (LD)beta * weight(i) * (3 * cF - 3 * uF + 9 * cu * cF);
+            ref[i] = (1 - (LD)omega) * f[i] + (LD)omega * feq + S;
+            mass_in += f[i];
+            mass_ref += ref[i];
+        }
+        collide_df(f, F[0], K);
+        LD mass_out = 0;
+        for (int i = 0; i < 19; i++) {
+            coll_abs = std::fmax(coll_abs, (double)(fabsl((LD)f[i] - ref[i]) / weight(i)));
+            mass_out += f[i];
+        }
+        mass_rel = std::fmax(mass_rel, (double)(fabsl(mass_out - mass_in) / mass_in));
+    }
+    std::printf("collide_abs_over_w %.3e\n", coll_abs);
+    std::printf("collide_mass_rel %.3e\n", mass_rel);
+    return 0;
+}
