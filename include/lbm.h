@@ -242,8 +242,7 @@ lbm_status lbm_get_info(lbm_ctx* ctx, int64_t* n_tiles, int64_t* n_nonsolid, int
 lbm_status lbm_save_state(lbm_ctx* ctx, void* blob, size_t* nbytes);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* blob, size_t nbytes);
 
-/* Allocation-free tile-map builder. The paper has no counterpart: it builds its tile
- * map on the host (Sec. 3.1, Algorithm 1) and says nothing about device memory policy.
+/* Allocation-free tile-map builder. The paper has no counterpart to this entry point.
  * It is for callers that cannot call cudaMalloc -- code running under a framework whose
  * caching allocator has reserved the device memory, or hosts that forbid allocation
  * after start-up -- and that already own their input and output buffers.
@@ -259,7 +258,9 @@ lbm_status lbm_load_state(lbm_ctx* ctx, const void* blob, size_t nbytes);
  *   stream     cudaStream_t for the work; the call synchronises it before returning.
  * Limits and errors: at most LBM_NOALLOC_MAX_TILES tiles in the tile grid (e.g. a
  * 1024 x 512 x 512 box); larger grids give LBM_EUNSUPPORTED before any device work.
- * NULL pointers or dimensions < 1 give LBM_EINVAL, node types outside 0..3 give
+ * The library cannot check the extent of the three device buffers: a host pointer or
+ * a buffer smaller than stated above is read or written out of bounds (the Python
+ * binding checks both before the call). NULL pointers or dimensions < 1 give LBM_EINVAL, node types outside 0..3 give
  * LBM_EINVAL after the kernels ran, CUDA failures LBM_ECUDA. There is no message string.
  * The first call on each device looks up the array's device address (with that device
  * current); make that first call before any stream capture. All calls share the one

@@ -222,9 +222,11 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     for (int a = 0; a < 3; a++)
         if ((periodic & (1u << a)) && dims[a] % lbm::TILE != 0)
             return fail(nullptr, LBM_EINVAL, "a periodic axis must be a multiple of 4");
-    const int64_t Tx = (nx + 3) / 4, Ty = (ny + 3) / 4, Tz = (nz + 3) / 4;
+    // widened before the rounding-up add: an axis near INT_MAX must not wrap
+    const int64_t Tx = ((int64_t)nx + 3) / 4, Ty = ((int64_t)ny + 3) / 4, Tz = ((int64_t)nz + 3) / 4;
+    if (Tx * Ty > 0x7fffffffll || Tx * Ty * Tz > 0x7fffffffll)   // each factor < 2^30: no overflow
+        return fail(nullptr, LBM_EINVAL, "tile grid larger than 2^31 tiles");
     const int64_t nT = Tx * Ty * Tz;
-    if (nT > 0x7fffffffll) return fail(nullptr, LBM_EINVAL, "tile grid larger than 2^31 tiles");
 
     lbm_ctx* c = new (std::nothrow) lbm_ctx();
     if (!c) return fail(nullptr, LBM_ENOMEM, "host allocation of the context failed");

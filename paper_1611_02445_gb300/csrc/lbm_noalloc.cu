@@ -35,8 +35,11 @@ extern "C" lbm_status lbm_build_tiles_noalloc(const uint8_t* node_type, int nx, 
                                               void* stream) {
     if (!node_type || !tile_map || !non_empty || !n_tiles) return LBM_EINVAL;
     if (nx < 1 || ny < 1 || nz < 1) return LBM_EINVAL;
-    const int64_t Tx = (nx + 3) / 4, Ty = (ny + 3) / 4, Tz = (nz + 3) / 4;
-    const int64_t nT = Tx * Ty * Tz;
+    // widened before the rounding-up add: nx near INT_MAX must not wrap
+    const int64_t Tx = ((int64_t)nx + 3) / 4, Ty = ((int64_t)ny + 3) / 4, Tz = ((int64_t)nz + 3) / 4;
+    if (Tx > kMaxTiles || Ty > kMaxTiles || Tz > kMaxTiles) return LBM_EUNSUPPORTED;
+    const int64_t nT = Tx * Ty * Tz;   // each factor <= 2^22, so no overflow
+    if (nT <= 0) return LBM_EINVAL;
     if (nT > kMaxTiles) return LBM_EUNSUPPORTED;   // beyond the static scratch: use lbm_create
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

@@ -268,15 +268,44 @@ def lbm_adjoint(ctx, T, ckpt_every, plane_x, dL_dg=None, want_dtau=True):
 NOALLOC_MAX_TILES = 1 << 22
 
 
+def _noalloc_buffer(name, x, dtypes, need):
+    """A device tensor the allocation-free builder may read or write: CUDA, one of the
+    given dtypes, contiguous and at least ``need`` elements. The C entry point takes raw
+    device pointers and cannot check their extent, so the binding checks it before any
+    launch."""
+    import torch
+    if not isinstance(x, torch.Tensor) or not x.is_cuda:
+        raise ValueError(f"lbm_build_tiles_noalloc: {name} must be a CUDA tensor (a host array "
+                         "would be read through a device pointer)")
+    if x.dtype not in dtypes:
+        raise ValueError(f"lbm_build_tiles_noalloc: {name} must have dtype "
+                         f"{' or '.join(str(d) for d in dtypes)}, not {x.dtype}")
+    if not x.is_contiguous():
+        raise ValueError(f"lbm_build_tiles_noalloc: {name} must be contiguous")
+    if x.numel() < need:
+        raise ValueError(f"lbm_build_tiles_noalloc: {name} has {x.numel()} elements, needs {need}")
+
+
 def lbm_build_tiles_noalloc(node_type, nx, ny, nz, tile_map, non_empty, stream=None):
     """Tile map into caller-owned device buffers, without any device allocation.
 
     For callers that cannot allocate device memory themselves (their framework's
-    allocator owns it, or allocation is forbidden after start-up): node_type, tile_map
-    (int32, one entry per tile of the grid) and non_empty (32-bit, as many entries) are
-    device tensors the caller already holds. Returns the number of kept tiles."""
+    allocator owns it, or allocation is forbidden after start-up): node_type (uint8,
+    nx*ny*nz), tile_map (int32, one entry per tile of the grid) and non_empty (32-bit,
+    as many entries) are contiguous CUDA tensors the caller already holds; their dtype
+    and size are checked here, before any launch. Returns the number of kept tiles."""
+    import torch
+    nx, ny, nz = int(nx), int(ny), int(nz)
+    if min(nx, ny, nz) < 1:
+        raise ValueError("lbm_build_tiles_noalloc: dimensions must be >= 1")
+    n_grid = ((nx + 3) // 4) * ((ny + 3) // 4) * ((nz + 3) // 4)
+    if n_grid <= NOALLOC_MAX_TILES:
+        _noalloc_buffer("node_type", node_type, (torch.uint8,), nx * ny * nz)
+        _noalloc_buffer("tile_map", tile_map, (torch.int32,), n_grid)
+        _noalloc_buffer("non_empty", non_empty, (torch.int32, torch.uint32), n_grid)
+    # larger grids are refused by the library before it touches any buffer
     n = ct.c_int64()
-    st = load().lbm_build_tiles_noalloc(_ptr(node_type), int(nx), int(ny), int(nz), _ptr(tile_map),
+    st = load().lbm_build_tiles_noalloc(_ptr(node_type), nx, ny, nz, _ptr(tile_map),
                                         _ptr(non_empty), ct.byref(n), _stream(stream))
     if st != 0:
         hint = {4: f"the tile grid exceeds {NOALLOC_MAX_TILES} tiles held by the static scratch; "

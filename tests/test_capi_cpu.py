@@ -56,3 +56,52 @@ def test_argument_validation_without_gpu(L):
     assert L.lbm_step(None, 1) == 1
     assert L.lbm_last_error(None) is not None
     L.lbm_destroy(None)
+
+
+def test_axis_near_int_max_is_rejected_before_any_device_work(L):
+    """Tile counts are formed in 64 bits: an axis of INT_MAX nodes must not wrap to a
+    negative tile count and reach a launch."""
+    big = 2 ** 31 - 1
+    nt = np.ones(8, np.uint8)
+    assert _create(L, nt, (big, big, big))[0] == 1                 # LBM_EINVAL: > 2^31 tiles
+    assert "2^31" in L.lbm_last_error(None).decode()
+    n = ct.c_int64(-5)
+    for dims in ((big, 1, 1), (1, big, 1), (big, big, big)):
+        st = L.lbm_build_tiles_noalloc(nt.ctypes.data, *dims, nt.ctypes.data, nt.ctypes.data, ct.byref(n), None)
+        assert st == 4                                           # LBM_EUNSUPPORTED, before device work
+    assert n.value == -5
+
+
+def test_noalloc_binding_checks_buffers_before_the_call():
+    """The C entry point takes raw device pointers; the binding refuses host arrays, CPU
+    tensors, wrong dtypes and undersized buffers before anything is launched."""
+    import torch
+    nx, ny, nz = 9, 8, 8                                          # 3 x 2 x 2 = 12 tiles
+    nt = torch.ones(nx * ny * nz, dtype=torch.uint8)
+    tm = torch.zeros(12, dtype=torch.int32)
+    ne = torch.zeros(12, dtype=torch.int32)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        lbm.lbm_build_tiles_noalloc(nt.numpy(), nx, ny, nz, tm, ne)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        lbm.lbm_build_tiles_noalloc(nt, nx, ny, nz, tm, ne)
+    with pytest.raises(ValueError, match="dimensions"):
+        lbm.lbm_build_tiles_noalloc(nt, 0, ny, nz, tm, ne)
+
+
+def test_noalloc_buffer_checks_on_fake_device_tensors(monkeypatch):
+    """Dtype, contiguity and size checks, with is_cuda faked (no GPU here): every case
+    raises in the binding, so the library is never called."""
+    import torch
+    monkeypatch.setattr(torch.Tensor, "is_cuda", property(lambda self: True))
+    monkeypatch.setattr(lbm, "load", lambda: pytest.fail("the library was called"))
+    nt = torch.ones(9 * 8 * 8, dtype=torch.uint8)                # 3 x 2 x 2 = 12 tiles
+    tm = torch.zeros(12, dtype=torch.int32)
+    cases = (((nt[1:], tm, tm), "node_type has 575 elements, needs 576"),
+             ((nt.to(torch.int32), tm, tm), "node_type must have dtype"),
+             ((nt, tm[1:], tm), "tile_map has 11 elements, needs 12"),
+             ((nt, tm.to(torch.int64), tm), "tile_map must have dtype"),
+             ((nt, tm, torch.zeros(24, dtype=torch.int32)[::2]), "non_empty must be contiguous"),
+             ((nt, tm, tm[1:]), "non_empty has 11 elements, needs 12"))
+    for (a, b, c), msg in cases:
+        with pytest.raises(ValueError, match=msg):
+            lbm.lbm_build_tiles_noalloc(a, 9, 8, 8, b, c)

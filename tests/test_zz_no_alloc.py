@@ -10,6 +10,7 @@ run every other test. It passes alone in a fresh process and after the other tes
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_1611_02445_gb300 import build as B
 from paper_1611_02445_gb300 import inputs as I
 from paper_1611_02445_gb300 import lbm
@@ -56,6 +57,8 @@ def test_noalloc_tiles_match_lbm_create_on_two_calls_in_a_row():
         tm_ref, ne_ref = _with_lbm_create(nt)
         assert np.array_equal(tm, tm_ref)      # integer work: bit-exact
         assert np.array_equal(ne, ne_ref)
+        tm_o, ne_o = O.tiling(nt)              # and against the oracle's Algorithm 1 directly
+        assert np.array_equal(tm, tm_o) and np.array_equal(ne, ne_o)
 
 
 def test_noalloc_error_flag_is_cleared_between_calls():
