@@ -34,15 +34,40 @@ struct DFConst {
     dfl Fy, Fz;          // uniform y, z force density
     dfl G9y, G9z;        // 9 beta F_y, 9 beta F_z
     dfl G3y, G3z;        // 3 beta w1 F_y, 3 beta w1 F_z
-    double Fy_d, Fz_d;   // F_y, F_z in FP64
+    int64_t Fy2q, Fz2q;  // F_y / 2, F_z / 2 in 2^-58 fixed point (truncated)
+    // The uniform x force (g[0]) and its terms, used when no per-node force field is set:
+    // F_x / 2 in fixed point, F_x, 9 beta F_x and 3 beta w1 F_x.
+    int64_t Fx2q;
+    dfl Fx, G9x, G3x;
 };
+
+// Force arguments of direction pair k of (1,3) (2,4) (5,6) (7,9) (8,10) (11,14) (12,13)
+// (15,18) (16,17) from the per-axis terms G9 = 9 beta F and G3 = 3 beta w1 F: a diagonal
+// pair's are the sums or differences of its axes', and its 3 beta w c.F is half the axis
+// value (w2 = w1 / 2). k is a constant after unrolling, so the switch folds away.
+LBM_DF_HD dfl df_g9(int k, dfl G9x, dfl G9y, dfl G9z) {
+    switch (k) {
+        case 0: return G9x;
+        case 1: return G9y;
+        case 2: return G9z;
+        case 3: return df_add(G9x, G9y);
+        case 4: return df_sub(G9y, G9x);
+        case 5: return df_add(G9x, G9z);
+        case 6: return df_sub(G9x, G9z);
+        case 7: return df_add(G9y, G9z);
+        default: return df_sub(G9y, G9z);
+    }
+}
+LBM_DF_HD dfl df_g3(int k, dfl G3x, dfl G3y, dfl G3z) {
+    return k < 3 ? df_g9(k, G3x, G3y, G3z) : df_scale2(df_g9(k, G3x, G3y, G3z), 0.5f);
+}
 
 LBM_DF_HD dfl df_split_host(double v) {
     const float h = (float)v;
     return df_make(h, (float)(v - (double)h));
 }
 
-LBM_DF_HD DFConst make_df_const(double omega, double beta, double Fy, double Fz) {
+LBM_DF_HD DFConst make_df_const(double omega, double beta, double Fx, double Fy, double Fz) {
     DFConst c;
     const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
     c.om1 = 1.0 - omega;
@@ -63,8 +88,12 @@ LBM_DF_HD DFConst make_df_const(double omega, double beta, double Fy, double Fz)
     c.G9z = df_split_host(9.0 * beta * Fz);
     c.G3y = df_split_host(3.0 * beta * w[1] * Fy);
     c.G3z = df_split_host(3.0 * beta * w[1] * Fz);
-    c.Fy_d = Fy;
-    c.Fz_d = Fz;
+    c.Fy2q = fix_from_double(Fy) >> 1;
+    c.Fz2q = fix_from_double(Fz) >> 1;
+    c.Fx2q = fix_from_double(Fx) >> 1;
+    c.Fx = df_split_host(Fx);
+    c.G9x = df_split_host(9.0 * beta * Fx);
+    c.G3x = df_split_host(3.0 * beta * w[1] * Fx);
     return c;
 }
 
@@ -88,7 +117,9 @@ LBM_DF_HD void df_pair(double& a, double& b, const DFConst& K, int k, dfl cj, df
 }
 
 // f: the 19 gathered populations of a fluid node, replaced by the post-collision ones.
-LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K) {
+// uniform_fx: Fx is the uniform force K was built with, so every term that depends on it
+// comes from K; otherwise (a per-node force field) they are formed here.
+LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool uniform_fx) {
     // exact moments in 64-bit fixed point, from pair sums s and differences d of
     // opposite directions (the FP64 pipe is kept for the final update)
     int64_t q[19];
@@ -103,11 +134,11 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K) {
     const int64_t jy = d24 + d79 + d810 + d1518 + d1617;
     const int64_t jz = d56 + d1114 - d1213 + d1518 - d1617;
     // j' = j + F/2 (F/2 in the same fixed point, truncated: |error| < 2^-58)
-    const dfl Jx = df_from_fix(jx + (fix_from_double(Fx) >> 1));
-    const dfl Jy = df_from_fix(jy + (fix_from_double(K.Fy_d) >> 1));
-    const dfl Jz = df_from_fix(jz + (fix_from_double(K.Fz_d) >> 1));
+    const dfl Jx = df_from_fix(jx + (uniform_fx ? K.Fx2q : fix_from_double(Fx) >> 1));
+    const dfl Jy = df_from_fix(jy + K.Fy2q);
+    const dfl Jz = df_from_fix(jz + K.Fz2q);
     const dfl inv = df_recip(df_from_fix(rho));
-    const dfl Fxd = df_from_double(Fx);
+    const dfl Fxd = uniform_fx ? K.Fx : df_from_double(Fx);
     // P = 1.5 omega |j'|^2 + 3 beta j'.F: the isotropic second-order part of every Y_i
     const dfl JJ = df_add(df_add(df_mul(Jx, Jx), df_mul(Jy, Jy)), df_mul(Jz, Jz));
     const dfl JF = df_add(df_add(df_mul(Jx, Fxd), df_mul(Jy, K.Fy)), df_mul(Jz, K.Fz));
@@ -134,24 +165,22 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K) {
 #else
     f[0] = std::fma(K.om1, f[0], df_to_double_pos(Y0));
 #endif
-    // force terms per axis; a diagonal pair's are sums, and its 3 beta w c.F is half the
-    // axis value (w2 = w1 / 2)
-    const dfl G9x = df_mul(K.b9, Fxd), G3x = df_mul(K.bw3, Fxd);
-    df_pair(f[1], f[3], K, 1, Jx, G9x, G3x, winv1, A[1], P);
-    df_pair(f[2], f[4], K, 1, Jy, K.G9y, K.G3y, winv1, A[1], P);
-    df_pair(f[5], f[6], K, 1, Jz, K.G9z, K.G3z, winv1, A[1], P);
-    df_pair(f[7], f[9], K, 2, df_add(Jx, Jy), df_add(G9x, K.G9y), df_scale2(df_add(G3x, K.G3y), 0.5f), winv2, A[2],
-            P);
-    df_pair(f[8], f[10], K, 2, df_sub(Jy, Jx), df_sub(K.G9y, G9x), df_scale2(df_sub(K.G3y, G3x), 0.5f), winv2,
-            A[2], P);
-    df_pair(f[11], f[14], K, 2, df_add(Jx, Jz), df_add(G9x, K.G9z), df_scale2(df_add(G3x, K.G3z), 0.5f), winv2,
-            A[2], P);
-    df_pair(f[12], f[13], K, 2, df_sub(Jx, Jz), df_sub(G9x, K.G9z), df_scale2(df_sub(G3x, K.G3z), 0.5f), winv2,
-            A[2], P);
-    df_pair(f[15], f[18], K, 2, df_add(Jy, Jz), df_add(K.G9y, K.G9z), df_scale2(df_add(K.G3y, K.G3z), 0.5f), winv2,
-            A[2], P);
-    df_pair(f[16], f[17], K, 2, df_sub(Jy, Jz), df_sub(K.G9y, K.G9z), df_scale2(df_sub(K.G3y, K.G3z), 0.5f), winv2,
-            A[2], P);
+    // Force arguments of the nine pairs, formed per pair from the per-axis terms (only
+    // those stay live through the pairs); the x terms come from K with a uniform force.
+    const dfl G9x = uniform_fx ? K.G9x : df_mul(K.b9, Fxd);
+    const dfl G3x = uniform_fx ? K.G3x : df_mul(K.bw3, Fxd);
+#define LBM_DF_PAIR(a, b, cls, k, cj, winv) \
+    df_pair(f[a], f[b], K, cls, cj, df_g9(k, G9x, K.G9y, K.G9z), df_g3(k, G3x, K.G3y, K.G3z), winv, A[cls], P)
+    LBM_DF_PAIR(1, 3, 1, 0, Jx, winv1);
+    LBM_DF_PAIR(2, 4, 1, 1, Jy, winv1);
+    LBM_DF_PAIR(5, 6, 1, 2, Jz, winv1);
+    LBM_DF_PAIR(7, 9, 2, 3, df_add(Jx, Jy), winv2);
+    LBM_DF_PAIR(8, 10, 2, 4, df_sub(Jy, Jx), winv2);
+    LBM_DF_PAIR(11, 14, 2, 5, df_add(Jx, Jz), winv2);
+    LBM_DF_PAIR(12, 13, 2, 6, df_sub(Jx, Jz), winv2);
+    LBM_DF_PAIR(15, 18, 2, 7, df_add(Jy, Jz), winv2);
+    LBM_DF_PAIR(16, 17, 2, 8, df_sub(Jy, Jz), winv2);
+#undef LBM_DF_PAIR
 }
 
 }  // namespace lbm

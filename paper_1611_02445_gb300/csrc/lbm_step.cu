@@ -234,7 +234,7 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
             zou_he<double, false>(v, ct, p);
             ct = LBM_FLUID;
         }
-        if (ct == LBM_FLUID) collide_df(v, (double)Fx, p.dfc);
+        if (ct == LBM_FLUID) collide_df(v, (double)Fx, p.dfc, !has_gf);
         else collide<R, false>(v, type, p, Fx, Fy, Fz);
     } else {
         collide<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);

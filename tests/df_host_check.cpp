@@ -69,7 +69,7 @@ int main() {
     for (int n = 0; n < 200000; n++) {
         const double tau = 0.51 + 1.5 * U(rng), omega = 1.0 / tau, beta = 1.0 - 0.5 / tau;
         const double F[3] = {1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1)};
-        const DFConst K = make_df_const(omega, beta, F[1], F[2]);
+        const DFConst K = make_df_const(omega, beta, F[0], F[1], F[2]);
         double f[19];
         const double u0[3] = {0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1)};
         const double rho0 = 0.9 + 0.2 * U(rng);
@@ -100,13 +100,18 @@ int main() {
             mass_in += f[i];
             mass_ref += ref[i];
         }
-        collide_df(f, F[0], K);
-        LD mass_out = 0;
-        for (int i = 0; i < 19; i++) {
-            coll_abs = std::fmax(coll_abs, (double)(fabsl((LD)f[i] - ref[i]) / weight(i)));
-            mass_out += f[i];
+        // both ways of forming the force terms: per launch (uniform force) and per node
+        for (int way = 0; way < 2; way++) {
+            double g[19];
+            for (int i = 0; i < 19; i++) g[i] = f[i];
+            collide_df(g, F[0], K, way == 0);
+            LD mass_out = 0;
+            for (int i = 0; i < 19; i++) {
+                coll_abs = std::fmax(coll_abs, (double)(fabsl((LD)g[i] - ref[i]) / weight(i)));
+                mass_out += g[i];
+            }
+            mass_rel = std::fmax(mass_rel, (double)(fabsl(mass_out - mass_in) / mass_in));
         }
-        mass_rel = std::fmax(mass_rel, (double)(fabsl(mass_out - mass_in) / mass_in));
     }
     std::printf("collide_abs_over_w %.3e\n", coll_abs);
     std::printf("collide_mass_rel %.3e\n", mass_rel);
