@@ -18,6 +18,7 @@ Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -133,6 +134,61 @@ def oracle_baseline(nt, steps_hint: int, budget_s: float, tau, g):
     return {"value": n * done / dt / 1e6, "unit": "MFLUPS", "cores": threads, "kind": "oracle",
             "sample": f"{done} full steps of the 256^3 porous workload ({n} non-solid nodes), "
                       f"dense FP64 oracle, OpenMP over z on {threads} threads, {dt:.1f} s"}
+
+
+def oracle_baseline_serial(nt, budget_s: float, tau, g):
+    """The same oracle on one host core: whole steps of the full workload until the
+    budget is spent (at least one)."""
+    from oracle import oracle as O
+    f = O.init(nt)
+    B = f.copy()
+    n = int(np.count_nonzero(nt))
+    t0 = time.perf_counter()
+    done = 0
+    while done == 0 or (time.perf_counter() - t0) < budget_s:
+        O.step(f, nt, 0b111, tau, g, nthreads=1, out=B)
+        f, B = B, f
+        done += 1
+    dt = time.perf_counter() - t0
+    return {"value": n * done / dt / 1e6, "unit": "MFLUPS", "cores": 1, "kind": "oracle",
+            "sample": f"{done} full steps of the 256^3 porous workload ({n} non-solid nodes), "
+                      f"dense FP64 oracle, serial, {dt:.1f} s"}
+
+
+def step_source_hash() -> str:
+    """Hash of the CUDA library sources; a stored DRAM traffic figure is valid only for
+    the sources it was captured with."""
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1611_02445_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(name.encode() + b"\0" + fh.read())
+    return h.hexdigest()[:16]
+
+
+def time_format(lbm, nt, dtype, tau, g, steps, warmup, stream):
+    """A short timed run of one storage format on the benchmark workload (CUDA events on
+    the launching stream around `steps` steps after `warmup`); MFLUPS and HBM fraction."""
+    import torch
+    L = lbm.Lattice(nt, dtype, 0b111, stream)
+    info = L.info()
+    L.set_params(tau, g)
+    L.init_equilibrium()
+    L.step(warmup)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    L.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    mass, _ = L.reduce()
+    L.close()
+    assert np.isfinite(mass)
+    n = info["n_nonsolid"]
+    value = n * steps / (ms * 1e-3) / 1e6
+    return value, ms / steps, n * 2 * 19 * BYTES_PER_VALUE[dtype] / (ms / steps * 1e-3) / 1e9
 
 
 def run_reference(args, nt, tau, g):
@@ -413,6 +469,7 @@ def main():
     ap.add_argument("--dtype", default="f64", choices=["f64", "f64n", "f32", "f16s", "f16sr"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-formats", action="store_true", help="skip the other storage formats' timed runs")
     ap.add_argument("--kernel", default="full", choices=["full", "propagate", "rw"],
                     help="the fused step, or one of the paper's calibration kernels (propagation "
                          "only, read/write only)")
@@ -482,10 +539,18 @@ def main():
 
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    # nvidia-smi samples every 200 ms, longer than a short timed region: the sampled
+    # window also covers about a second of untimed steps right before it, under the same load
+    ev0.record(stream)
+    L.step_kernel(kind, 3)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    soak = max(1, int(1000.0 / max(ev0.elapsed_time(ev1) / 3, 1e-3)))
     sampler = ClockSampler(local_rank)
     barrier()
     sampler.start()
     time.sleep(0.3)
+    L.step_kernel(kind, soak)
     ev0.record(stream)
     L.step_kernel(kind, args.steps)
     ev1.record(stream)
@@ -534,10 +599,18 @@ def main():
                 "fp64_flops_per_node_update": flops_per_node,
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s", "frac": achieved_gbs / hbm_peak}}
     full_size = args.kernel == "full" and args.model == "bgk" and args.size == 256
-    roof["traffic"] = TRAFFIC_PER_LAUNCH_256.get(args.dtype) if full_size else None
-    if roof["traffic"] is not None:
+    captured = TRAFFIC_PER_LAUNCH_256.get(args.dtype) if full_size else None
+    src_hash = step_source_hash()
+    roof["sources"] = src_hash
+    if captured is not None and TRAFFIC_PER_LAUNCH_256["sources"] == src_hash:
+        roof["traffic"] = captured
         roof["traffic_source"] = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of this launch (porous 256^3 "
-                                  "pack), mean of two captured launches")
+                                  f"pack), mean of two captured launches, library sources {src_hash}")
+        roof["traffic_per_node"] = captured / n_nonsolid
+        roof["traffic_over_algorithmic"] = captured / alg_bytes
+    elif captured is not None:
+        roof["traffic_source"] = (f"null: captured for library sources {TRAFFIC_PER_LAUNCH_256['sources']}, "
+                                  f"these are {src_hash}")
 
     line = {"metric": METRIC, "value": value, "unit": "MFLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -553,11 +626,32 @@ def main():
                        "l2_policy": "inputs larger than L2 (two population copies of "
                                     f"{info['copy_bytes'] / 1e9:.2f} GB each vs 126 MB L2)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": roof, "gpu_launches": args.steps, "clocks": clocks,
+            "roofline": roof, "gpu_launches": args.steps,
+            "clocks": dict(clocks or {}, window=f"{soak} untimed steps right before the timed region, and the region"),
             "reduction": {"ms": red_ms, "bytes": info["copy_bytes"],
                           "gbs": info["copy_bytes"] / (red_ms * 1e-3) / 1e9,
                           "what": "lbm_reduce: FP64 mass and momentum over one copy, best of 5 calls, "
                                   "host wall time including the 32-byte result copy"}}
+
+    # the other storage formats on the same workload, timed alike (the headline is f64)
+    if args.kernel == "full" and args.model == "bgk" and not args.no_formats:
+        L.close()
+        fsteps = max(args.steps, 50)
+        formats = {}
+        for dt in ("f64n", "f32", "f16s"):
+            if dt == args.dtype:
+                continue
+            v, ms_step, gbs = time_format(lbm, nt, dt, tau, g, fsteps, args.warmup, stream)
+            entry = {"value": v, "ms_per_step": ms_step, "frac": gbs / hbm_peak, "speedup_over_headline": v / value,
+                     "steps": fsteps}
+            if dt == "f64n":
+                tf = n_nonsolid * FP64_FLOPS_PER_NODE / (ms_step * 1e-3) / 1e12
+                entry["fp64_alu"] = {"achieved_tflops": tf, "peak_tflops": 152 * 2 * 2 * 2.07e9 / 1e12,
+                                     "frac": tf / (152 * 2 * 2 * 2.07e9 / 1e12)}
+            formats[dt] = entry
+        line["formats"] = {"headline": args.dtype, "unit": "MFLUPS", "frac_of": "measured hbm_gbs, algorithmic bytes",
+                           "what": "the same workload and step with other storage formats, CUDA events around "
+                                   f"{fsteps} steps after {args.warmup} warm-up steps", **formats}
 
     # end to end through the public API: host node types in, host results out
     if not args.no_e2e:
@@ -591,6 +685,7 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # about 15 s of oracle steps on the host cores (a bounded sample of the workload)
         line["cpu_baseline"] = oracle_baseline(nt, 1000, 15.0, tau, g)
+        line["cpu_baseline_serial"] = oracle_baseline_serial(nt, 5.0, tau, g)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -610,8 +705,10 @@ FP64_FLOPS_PER_NODE = 331
 
 # DRAM bytes (read + write) of one step launch on the porous 256^3 pack, from a one-pass
 # ncu capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean of
-# two launches after three warm-up steps); absent where not captured for the current kernel.
-TRAFFIC_PER_LAUNCH_256 = {"f64": 1989303168 + 1107922432,
+# two launches after three warm-up steps), with the hash (step_source_hash) of the library
+# sources they were captured with; the bench reports them only while the sources match.
+TRAFFIC_PER_LAUNCH_256 = {"sources": "",
+                          "f64": 1989303168 + 1107922432,
                           "f32": 855424256 + 578127104,
                           "f16s": 822345472 + 329302144}
 

@@ -242,6 +242,66 @@ lbm_status lbm_get_info(lbm_ctx* ctx, int64_t* n_tiles, int64_t* n_nonsolid, int
 lbm_status lbm_save_state(lbm_ctx* ctx, void* blob, size_t* nbytes);
 lbm_status lbm_load_state(lbm_ctx* ctx, const void* blob, size_t nbytes);
 
+/* ------------------------------------------------------------------------------------
+ * Domain decomposition into z-slabs with a halo exchange (the paper names multi-GPU
+ * execution as future work, Sec. 5; the step itself is unchanged, Sec. 3.4). Each rank
+ * owns a contiguous range of tile planes along z, the outermost axis of the tile order
+ * (Sec. 3.1), so its tiles and its ghost tiles are contiguous rank ranges. Before every
+ * step the populations that cross a cut -- the five directions with c_z = +1 or -1 --
+ * of the boundary tiles are copied into the neighbouring slab's ghost plane; mass and
+ * momentum are summed over ranks in FP64. The transport between ranks is the caller's
+ * (the Python binding uses torch.distributed). */
+
+/* Split the tile planes along z into nranks contiguous slabs of about equal numbers of
+ * non-solid nodes. Host only, no GPU needed.
+ *   node_type    host, nx*ny*nz bytes (the whole domain).
+ *   plane_begin  host, nranks + 1 ints: rank r owns tile planes [plane_begin[r],
+ *                plane_begin[r+1]); plane_begin[0] = 0, plane_begin[nranks] = ceil(nz/4).
+ * LBM_EINVAL unless 1 <= nranks <= ceil(nz/4); every slab gets at least one plane. */
+lbm_status lbm_partition_z(const uint8_t* node_type, int nx, int ny, int nz, int nranks, int* plane_begin);
+
+/* The node types of a slab's box: its own tile planes [plane_begin, plane_end) plus one
+ * ghost tile plane below and above where the domain continues there (always on a
+ * periodic z axis, else not at the domain's ends); no ghost planes if the slab is the
+ * whole domain. Host only, no GPU needed.
+ *   sub          host, nx*ny*(*nz_sub) bytes, or NULL to ask only for the sizes; padding
+ *                nodes beyond nz are solid.
+ *   nz_sub       receives the box's z extent (4 per tile plane).
+ *   ghost_lo/hi  receive 1 for a ghost plane at the bottom / top of the box, else 0
+ *                (either may be NULL).
+ * LBM_EINVAL for an empty or out-of-range plane range or a periodic z axis that is not a
+ * multiple of 4. */
+lbm_status lbm_slab_geometry(const uint8_t* node_type, int nx, int ny, int nz, unsigned periodic, int plane_begin,
+                             int plane_end, uint8_t* sub, int* nz_sub, int* ghost_lo, int* ghost_hi);
+
+/* A context for one slab: lbm_create on the slab's box (lbm_slab_geometry), periodic in
+ * x and y as given, its ghost planes standing for the rest of the domain along z. The
+ * step, lbm_reduce and lbm_macroscopic cover the own tiles only; lbm_init_equilibrium,
+ * lbm_set_f / lbm_get_f / lbm_get_f_box and lbm_save_state cover the whole box, in box
+ * coordinates (box z = 0 is global node z = 4 (plane_begin - ghost_lo), wrapped on a
+ * periodic axis). lbm_get_info counts the own non-solid nodes. lbm_adjoint returns
+ * LBM_EUNSUPPORTED. A slab that is the whole domain is a plain lbm_create context.
+ *   node_type    host, the whole domain's nx*ny*nz node types.
+ * Other arguments and errors as lbm_create and lbm_slab_geometry. */
+lbm_status lbm_create_slab(const uint8_t* node_type, int nx, int ny, int nz, int tile, lbm_dtype dtype,
+                           unsigned periodic, int plane_begin, int plane_end, void* stream, lbm_ctx** out);
+
+/* Halo of a slab context, on its current population copy (call between steps).
+ *   side  0: the bottom of the box, 1: the top.
+ *   lbm_halo_pack copies the populations the neighbouring slab on that side reads from
+ *   this slab's boundary plane (side 0: the lowest own plane, directions with c_z = -1;
+ *   side 1: the highest, c_z = +1) into buf, [direction][tile][64] in the stored format;
+ *   lbm_halo_unpack copies such a buffer, packed by that neighbour on the opposite side,
+ *   into the ghost plane on this side. The two planes hold the same kept tiles in the
+ *   same order, since both slabs were cut from the same geometry.
+ *   lbm_halo_bytes gives the size of the buffer pack (pack = 1) or unpack (pack = 0)
+ *   uses on that side: 5 * 64 * (bytes per value) per tile of the plane.
+ *   buf   device pointer, on the context's stream; the copies are queued, not awaited.
+ * LBM_ESTATE if the box has no ghost plane on that side or no state is set. */
+lbm_status lbm_halo_bytes(lbm_ctx* ctx, int side, int pack, size_t* bytes);
+lbm_status lbm_halo_pack(lbm_ctx* ctx, int side, void* buf);
+lbm_status lbm_halo_unpack(lbm_ctx* ctx, int side, const void* buf);
+
 /* Allocation-free tile-map builder. The paper has no counterpart to this entry point.
  * It is for callers that cannot call cudaMalloc -- code running under a framework whose
  * caching allocator has reserved the device memory, or hosts that forbid allocation

@@ -285,9 +285,9 @@ namespace {
 
 struct DevBuf {
     void* p = nullptr;
-    cudaError_t alloc(size_t n) { return cudaMalloc(&p, std::max<size_t>(n, 16)); }
+    cudaError_t alloc(size_t n) { return dmalloc(&p, std::max<size_t>(n, 16)); }
     ~DevBuf() {
-        if (p) cudaFree(p);
+        if (p) dfree(p);
     }
 };
 
@@ -303,7 +303,7 @@ cudaError_t run_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, dou
     const int n_ck = (T + K - 1) / K;
     const int seg_len = std::min(K, T);
     const size_t mu_bytes = (size_t)c->n_tiles * Q * SLOTS * sizeof(R);
-    const int adj_blocks = (int)std::max<int64_t>(1, (c->n_nonsolid + ADJ_THREADS - 1) / ADJ_THREADS);
+    const int adj_blocks = (int)std::max<int64_t>(1, (c->n_own_nonsolid + ADJ_THREADS - 1) / ADJ_THREADS);
     const int nbl = (int)std::max<int64_t>(1, std::min<int64_t>((n_slots + LOSS_THREADS - 1) / LOSS_THREADS, 152 * 4));
     const size_t N = (size_t)c->nx * c->ny * c->nz;
     // every buffer is allocated before any work, so that a failed allocation leaves the
@@ -371,7 +371,7 @@ cudaError_t run_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, dou
         for (int t = t1 - 1; t >= t0; t--) {
             k_adjoint<DT><<<adj_blocks, ADJ_THREADS, 0, c->stream>>>(
                 reinterpret_cast<const TT*>(sb + copy * (t - t0)), mu[mcur], direct ? 1 : 0, mu[1 - mcur], c->nbr,
-                c->fword, c->fidx, c->gfield, c->n_nonsolid, c->p, static_cast<double*>(gbar.p),
+                c->fword, c->fidx, c->gfield, c->n_own_nonsolid, c->p, static_cast<double*>(gbar.p),
                 static_cast<double*>(taup.p));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             mcur ^= 1;

@@ -4,6 +4,7 @@
 // kernel launches on the context's stream, and host <-> device copies. Every step of
 // the computation runs in the kernels of lbm_tiles.cu and lbm_step.cu.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,10 +14,34 @@
 
 #include "lbm_collide.cuh"
 #include "lbm_internal.cuh"
+#include "../../include/lbm_testing.h"
 
 namespace lbm {
 int reduce_blocks(int64_t n_tiles);
 }
+
+namespace lbm {
+
+namespace {
+std::atomic<int64_t> g_live_allocs{0};
+std::atomic<int64_t> g_fail_after{-1};   // allocations left before an injected failure; < 0: none
+}  // namespace
+
+cudaError_t dmalloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (g_fail_after.load() >= 0 && g_fail_after.fetch_sub(1) == 0) return cudaErrorMemoryAllocation;
+    const cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaSuccess) g_live_allocs.fetch_add(1);
+    return e;
+}
+
+void dfree(void* p) {
+    if (!p) return;
+    cudaFree(p);
+    g_live_allocs.fetch_sub(1);
+}
+
+}  // namespace lbm
 
 namespace {
 
@@ -60,7 +85,7 @@ template <typename T>
 cudaError_t dev_alloc(T** p, size_t count) {
     *p = nullptr;
     if (count == 0) count = 1;
-    return cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T));
+    return lbm::dmalloc(reinterpret_cast<void**>(p), count * sizeof(T));
 }
 
 void drop_graphs(lbm_ctx* c) {
@@ -103,9 +128,9 @@ void free_all(lbm_ctx* c) {
     drop_graphs(c);
     void* bufs[] = {c->tile_map, c->non_empty, c->nbr,    c->smask,  c->tflags, c->ntype,    c->nword,
                     c->groups,   c->fword,     c->fidx,   c->gfield, c->gfield_c, c->f[0], c->f[1],
-                    c->partials, c->d_out, c->seed, c->gfill_rng, c->gfill};
+                    c->partials, c->d_out, c->seed, c->gfill_rng, c->gfill, c->check};
     for (void* b : bufs)
-        if (b) cudaFree(b);
+        if (b) lbm::dfree(b);
     c->tile_map = nullptr;
     c->non_empty = nullptr;
     c->nbr = nullptr;
@@ -124,6 +149,7 @@ void free_all(lbm_ctx* c) {
     c->partials = nullptr;
     c->d_out = nullptr;
     c->seed = nullptr;
+    c->check = nullptr;
 }
 
 // Device-side check that every neighbour entry is -1 or a valid rank.
@@ -184,6 +210,25 @@ void set_mrt_constants(lbm_ctx* c) {
     }
 }
 
+// The checked build's error word after a run of steps: any failed index check makes the
+// context fail with LBM_EINTERNAL (the kernel skipped the access it could not make). The
+// normal build has no error word and returns at once.
+lbm_status read_check(lbm_ctx* c) {
+    if (!c->check) return LBM_OK;
+    unsigned long long word = 0;
+    LBM_CUDA(c, cudaMemcpyAsync(&word, c->check, sizeof(word), cudaMemcpyDeviceToHost, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (word == 0) return LBM_OK;
+    static const char* what[] = {"?", "work-group header or fill range out of range", "node tile not in its group",
+                                 "neighbour rank of a pulled direction not a kept tile",
+                                 "fill entry tile not in its group"};
+    const unsigned code = (unsigned)(word >> 56);
+    return fail(c, LBM_EINTERNAL,
+                std::string("checked build: step kernel index check failed (") + what[code < 5 ? code : 0] +
+                    ", code " + std::to_string(code) + ", value " + std::to_string(word & 0x00ffffffffffffffull) +
+                    "); the access was skipped");
+}
+
 }  // namespace
 
 extern "C" {
@@ -202,8 +247,11 @@ lbm_status lbm_set_stream(lbm_ctx* ctx, void* stream) {
     return LBM_OK;
 }
 
-lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, int nz, int tile,
-                      lbm_dtype dtype, unsigned periodic, void* stream, lbm_ctx** out) {
+// lbm_create's body. ghost_lo / ghost_hi: the box's first / last tile plane along z is a
+// ghost plane of a slab context (its tiles get no work group and are not reduced).
+static lbm_status create_impl(const uint8_t* node_type, int on_device, int nx, int ny, int nz, int tile,
+                              lbm_dtype dtype, unsigned periodic, void* stream, int ghost_lo, int ghost_hi,
+                              lbm_ctx** out) {
     g_create_err.clear();
     if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
     *out = nullptr;
@@ -244,11 +292,11 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     int64_t* d_count = nullptr;
     int* d_bad = nullptr;
     auto cleanup = [&]() {
-        if (!on_device && d_nt) cudaFree(d_nt);
-        if (d_flag) cudaFree(d_flag);
-        if (d_sums) cudaFree(d_sums);
-        if (d_count) cudaFree(d_count);
-        if (d_bad) cudaFree(d_bad);
+        if (!on_device && d_nt) lbm::dfree(d_nt);
+        if (d_flag) lbm::dfree(d_flag);
+        if (d_sums) lbm::dfree(d_sums);
+        if (d_count) lbm::dfree(d_count);
+        if (d_bad) lbm::dfree(d_bad);
     };
     auto bail = [&](lbm_status s2) {
         g_create_err = c->err.empty() ? std::string("lbm_create failed") : c->err;
@@ -308,8 +356,12 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     LBM_CREATE_CUDA(dev_alloc(&c->ntype, (size_t)count * lbm::SLOTS));
     LBM_CREATE_CUDA(dev_alloc(&c->partials, (size_t)c->n_partials * 4));
     LBM_CREATE_CUDA(dev_alloc(&c->d_out, 8));
-    LBM_CREATE_CUDA(cudaMalloc(&c->f[0], std::max<size_t>(copy_bytes, 16)));
-    LBM_CREATE_CUDA(cudaMalloc(&c->f[1], std::max<size_t>(copy_bytes, 16)));
+    LBM_CREATE_CUDA(lbm::dmalloc(&c->f[0], std::max<size_t>(copy_bytes, 16)));
+    LBM_CREATE_CUDA(lbm::dmalloc(&c->f[1], std::max<size_t>(copy_bytes, 16)));
+#ifdef LBM_CHECKED
+    LBM_CREATE_CUDA(dev_alloc(&c->check, 1));
+    LBM_CREATE_CUDA(cudaMemsetAsync(c->check, 0, sizeof(unsigned long long), c->stream));
+#endif
     if (sr) {
         LBM_CREATE_CUDA(dev_alloc(&c->seed, 2));
         LBM_CREATE_CUDA(cudaMemsetAsync(c->seed, 0, 2 * sizeof(uint32_t), c->stream));
@@ -337,9 +389,27 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
         // them and at most GROUP_MAX_NODES (FP64: GROUP_MAX_NODES_F64) non-solid nodes, so that threads map to
         // non-solid nodes only. Built once on the host from the per-node words.
         std::vector<uint32_t> words((size_t)count * lbm::SLOTS);
+        std::vector<uint32_t> tiles_h((size_t)count);
         if (count > 0) {
             LBM_CREATE_CUDA(cudaMemcpyAsync(words.data(), c->nword, words.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+            LBM_CREATE_CUDA(cudaMemcpyAsync(tiles_h.data(), c->non_empty, tiles_h.size() * 4, cudaMemcpyDeviceToHost,
+                                            c->stream));
             LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
+        }
+        // own tiles: kept tiles outside the ghost planes; the ranks follow the z-outermost
+        // discovery order, so each plane is one contiguous range of ranks
+        const int64_t plane = (int64_t)c->Tx * c->Ty;
+        c->ghost_lo = ghost_lo;
+        c->ghost_hi = ghost_hi;
+        c->own_k0 = 0;
+        c->own_k1 = count;
+        c->bnd_lo = c->bnd_hi = 0;
+        for (int64_t r = 0; r < count; r++) {
+            const int64_t tz = (int64_t)tiles_h[r] / plane;
+            if (tz < ghost_lo) c->own_k0 = r + 1;
+            if (tz >= c->Tz - ghost_hi && c->own_k1 == count) c->own_k1 = r;
+            if (tz == ghost_lo) c->bnd_lo++;
+            if (tz == c->Tz - 1 - ghost_hi) c->bnd_hi++;
         }
         std::vector<int4> groups;
         std::vector<uint32_t> fw, fi;
@@ -352,15 +422,15 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
         const int max_tiles = dtype == LBM_F64 ? lbm::GROUP_MAX_TILES_F64 : lbm::GROUP_MAX_TILES_4B;
         fw.reserve((size_t)nonsolid);
         fi.reserve((size_t)nonsolid);
-        int64_t k = 0;
-        while (k < count) {
+        int64_t k = c->own_k0;
+        while (k < c->own_k1) {
             int4 g;
             g.x = (int)k;
             g.y = 0;
             g.z = (int)fw.size();
             g.w = 0;
             const size_t fill0 = fill.size();
-            while (k < count && g.y < max_tiles) {
+            while (k < c->own_k1 && g.y < max_tiles) {
                 int cnt = 0;
                 for (int sl = 0; sl < lbm::SLOTS; sl++) cnt += (words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) != 0;
                 if (g.w + cnt > max_nodes) break;
@@ -385,10 +455,12 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
             groups.push_back(g);
             fill_rng.push_back(make_int2((int)fill0, (int)(fill.size() - fill0)));
         }
-        if ((int64_t)fw.size() != c->n_nonsolid) {
+        // the step updates the own tiles' nodes: in a slab context fewer than the box holds
+        if (ghost_lo == 0 && ghost_hi == 0 && (int64_t)fw.size() != c->n_nonsolid) {
             fail(c, LBM_EINTERNAL, "non-solid node count mismatch while building work groups");
             return bail(LBM_EINTERNAL);
         }
+        c->n_own_nonsolid = (int64_t)fw.size();
         c->n_groups = (int64_t)groups.size();
         c->n_fill = (int64_t)fill.size();
         LBM_CREATE_CUDA(dev_alloc(&c->gfill_rng, fill_rng.size()));
@@ -412,10 +484,126 @@ lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, i
     c->p.omega = 1.0;
     c->p.beta = 0.5;
     c->p.rho_out = 1.0;
+    c->p.n_tiles = c->n_tiles;
+    c->p.n_lanes = c->n_own_nonsolid;
+    c->p.n_fill = c->n_fill;
+    c->p.check = c->check;
     cleanup();
 #undef LBM_CREATE_CUDA
     *out = c;
     return LBM_OK;
+}
+
+lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, int nz, int tile,
+                      lbm_dtype dtype, unsigned periodic, void* stream, lbm_ctx** out) {
+    return create_impl(node_type, on_device, nx, ny, nz, tile, dtype, periodic, stream, 0, 0, out);
+}
+
+// ------------------------------------------------------------- slabs and their halos
+lbm_status lbm_partition_z(const uint8_t* node_type, int nx, int ny, int nz, int nranks, int* plane_begin) {
+    g_create_err.clear();
+    if (!node_type || !plane_begin) return fail(nullptr, LBM_EINVAL, "node_type and plane_begin are required");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "dimensions must be >= 1");
+    const int Tz = (int)(((int64_t)nz + 3) / 4);
+    if (nranks < 1 || nranks > Tz) return fail(nullptr, LBM_EINVAL, "need 1 <= nranks <= ceil(nz / 4)");
+    const int64_t layer = (int64_t)nx * ny;
+    std::vector<int64_t> cum((size_t)Tz + 1, 0);   // non-solid nodes below each tile plane
+    for (int P = 0; P < Tz; P++) {
+        int64_t cnt = 0;
+        for (int64_t z = 4LL * P; z < std::min<int64_t>(4LL * P + 4, nz); z++)
+            for (int64_t i = 0; i < layer; i++) cnt += node_type[z * layer + i] != 0;
+        cum[P + 1] = cum[P] + cnt;
+    }
+    plane_begin[0] = 0;
+    plane_begin[nranks] = Tz;
+    for (int r = 1; r < nranks; r++) {
+        // the first plane whose nodes below reach r / nranks of the total, keeping at
+        // least one plane for every rank
+        const double target = (double)cum[Tz] * r / nranks;
+        int P = plane_begin[r - 1] + 1;
+        while (P < Tz - (nranks - r) && (double)cum[P] < target) P++;
+        plane_begin[r] = P;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_slab_geometry(const uint8_t* node_type, int nx, int ny, int nz, unsigned periodic, int plane_begin,
+                             int plane_end, uint8_t* sub, int* nz_sub, int* ghost_lo, int* ghost_hi) {
+    g_create_err.clear();
+    if (!node_type || !nz_sub) return fail(nullptr, LBM_EINVAL, "node_type and nz_sub are required");
+    if (nx < 1 || ny < 1 || nz < 1) return fail(nullptr, LBM_EINVAL, "dimensions must be >= 1");
+    if ((periodic & LBM_PERIODIC_Z) && nz % 4) return fail(nullptr, LBM_EINVAL, "a periodic axis must be a multiple of 4");
+    const int Tz = (int)(((int64_t)nz + 3) / 4);
+    if (plane_begin < 0 || plane_end > Tz || plane_begin >= plane_end)
+        return fail(nullptr, LBM_EINVAL, "need 0 <= plane_begin < plane_end <= ceil(nz / 4)");
+    const bool whole = plane_begin == 0 && plane_end == Tz;
+    const bool pz = (periodic & LBM_PERIODIC_Z) != 0;
+    const int gl = !whole && (plane_begin > 0 || pz) ? 1 : 0;
+    const int gh = !whole && (plane_end < Tz || pz) ? 1 : 0;
+    const int planes = plane_end - plane_begin + gl + gh;
+    *nz_sub = 4 * planes;
+    if (ghost_lo) *ghost_lo = gl;
+    if (ghost_hi) *ghost_hi = gh;
+    if (!sub) return LBM_OK;
+    const int64_t layer = (int64_t)nx * ny;
+    for (int q = 0; q < planes; q++) {
+        const int P = ((plane_begin - gl + q) % Tz + Tz) % Tz;   // wraps only on a periodic z axis
+        for (int j = 0; j < 4; j++) {
+            uint8_t* dst = sub + (int64_t)(4 * q + j) * layer;
+            const int64_t z = 4LL * P + j;
+            if (z < nz) std::memcpy(dst, node_type + z * layer, (size_t)layer);
+            else std::memset(dst, 0, (size_t)layer);                // padding: solid
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_create_slab(const uint8_t* node_type, int nx, int ny, int nz, int tile, lbm_dtype dtype,
+                           unsigned periodic, int plane_begin, int plane_end, void* stream, lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_EINVAL, "out is NULL");
+    *out = nullptr;
+    int nzs = 0, gl = 0, gh = 0;
+    lbm_status st = lbm_slab_geometry(node_type, nx, ny, nz, periodic, plane_begin, plane_end, nullptr, &nzs, &gl, &gh);
+    if (st != LBM_OK) return st;
+    if (gl == 0 && gh == 0) return lbm_create(node_type, 0, nx, ny, nz, tile, dtype, periodic, stream, out);
+    std::vector<uint8_t> sub;
+    try {
+        sub.resize((size_t)nx * ny * nzs);
+    } catch (...) {
+        return fail(nullptr, LBM_ENOMEM, "host allocation of the slab geometry failed");
+    }
+    lbm_slab_geometry(node_type, nx, ny, nz, periodic, plane_begin, plane_end, sub.data(), &nzs, &gl, &gh);
+    // x and y keep their boundary conditions; along z the ghost planes stand for the rest
+    st = create_impl(sub.data(), 0, nx, ny, nzs, tile, dtype, periodic & ~(unsigned)LBM_PERIODIC_Z, stream, gl, gh,
+                     out);
+    if (st == LBM_OK) (*out)->z_plane0 = plane_begin - gl;
+    return st;
+}
+
+lbm_status lbm_halo_bytes(lbm_ctx* c, int side, int pack, size_t* bytes) {
+    LBM_CHECK_CTX(c);
+    if ((side != 0 && side != 1) || !bytes) return fail(c, LBM_EINVAL, "side must be 0 or 1, bytes non-NULL");
+    const bool ghost = side == 0 ? c->ghost_lo : c->ghost_hi;
+    const int64_t n = !ghost ? 0 : pack ? (side == 0 ? c->bnd_lo : c->bnd_hi)
+                                        : (side == 0 ? c->own_k0 : c->n_tiles - c->own_k1);
+    *bytes = (size_t)n * 5 * lbm::SLOTS * lbm::dtype_size(c->dtype);
+    return LBM_OK;
+}
+
+static lbm_status halo_io(lbm_ctx* c, int side, int pack, void* buf) {
+    LBM_CHECK_CTX(c);
+    if (side != 0 && side != 1) return fail(c, LBM_EINVAL, "side must be 0 or 1");
+    if (!(side == 0 ? c->ghost_lo : c->ghost_hi)) return fail(c, LBM_ESTATE, "no ghost plane on that side");
+    if (!buf) return fail(c, LBM_EINVAL, "buf is NULL");
+    if (!c->state_set) return fail(c, LBM_ESTATE, "no state");
+    LBM_CUDA(c, lbm::launch_halo(c, side, pack, buf));
+    return LBM_OK;
+}
+
+lbm_status lbm_halo_pack(lbm_ctx* c, int side, void* buf) { return halo_io(c, side, 1, buf); }
+
+lbm_status lbm_halo_unpack(lbm_ctx* c, int side, const void* buf) {
+    return halo_io(c, side, 0, const_cast<void*>(buf));
 }
 
 lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double* g_field,
@@ -428,15 +616,15 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
         const int64_t N = (int64_t)c->nx * c->ny * c->nz;
         const size_t gsize = c->dtype == LBM_F64 ? 8 : 4;
         const size_t gbytes = (size_t)std::max<int64_t>(c->n_tiles, 1) * lbm::SLOTS * gsize;
-        if (!c->gfield) LBM_CUDA(c, cudaMalloc(&c->gfield, gbytes));
-        if (!c->gfield_c) LBM_CUDA(c, cudaMalloc(&c->gfield_c, (size_t)std::max<int64_t>(c->n_nonsolid, 1) * gsize));
+        if (!c->gfield) LBM_CUDA(c, lbm::dmalloc(&c->gfield, gbytes));
+        if (!c->gfield_c) LBM_CUDA(c, lbm::dmalloc(&c->gfield_c, (size_t)std::max<int64_t>(c->n_own_nonsolid, 1) * gsize));
         const double* d_dense = g_field;
         double* tmp = nullptr;
         if (!g_field_on_device) {
             LBM_CUDA(c, dev_alloc(&tmp, (size_t)N));
             cudaError_t e = cudaMemcpyAsync(tmp, g_field, (size_t)N * sizeof(double), cudaMemcpyHostToDevice, c->stream);
             if (e != cudaSuccess) {
-                cudaFree(tmp);
+                lbm::dfree(tmp);
                 return cuda_fail(c, "cudaMemcpyAsync(g_field)", e);
             }
             d_dense = tmp;
@@ -445,14 +633,14 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
         if (e == cudaSuccess && c->n_tiles > 0) e = lbm::launch_gfield_compact(c);
         if (tmp) {
             cudaError_t e2 = cudaStreamSynchronize(c->stream);
-            cudaFree(tmp);
+            lbm::dfree(tmp);
             if (e == cudaSuccess) e = e2;
         }
         if (e != cudaSuccess) return cuda_fail(c, "set g_field", e);
     } else if (c->gfield) {
         LBM_CUDA(c, cudaStreamSynchronize(c->stream));
-        cudaFree(c->gfield);
-        cudaFree(c->gfield_c);
+        lbm::dfree(c->gfield);
+        lbm::dfree(c->gfield_c);
         c->gfield = nullptr;
         c->gfield_c = nullptr;
     }
@@ -564,7 +752,7 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
         LBM_CUDA(c, lbm::launch_step(c, c->f[c->cur], c->f[1 - c->cur]));
         c->cur ^= 1;
     }
-    return LBM_OK;
+    return read_check(c);
 }
 
 lbm_status lbm_step_kernel(lbm_ctx* c, int kind, int n) {
@@ -576,7 +764,7 @@ lbm_status lbm_step_kernel(lbm_ctx* c, int kind, int n) {
         LBM_CUDA(c, lbm::launch_step_kind(c, kind, c->f[c->cur], c->f[1 - c->cur]));
         c->cur ^= 1;
     }
-    return LBM_OK;
+    return read_check(c);
 }
 
 lbm_status lbm_reduce(lbm_ctx* c, double* mass, double* momentum) {
@@ -605,7 +793,7 @@ lbm_status lbm_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64, int on_d
     void* d_u = u;
     void* tmp = nullptr;
     if (!on_device) {
-        LBM_CUDA(c, cudaMalloc(&tmp, (size_t)N * 4 * es));
+        LBM_CUDA(c, lbm::dmalloc(&tmp, (size_t)N * 4 * es));
         d_rho = tmp;
         d_u = static_cast<char*>(tmp) + (size_t)N * es;
     }
@@ -619,7 +807,7 @@ lbm_status lbm_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64, int on_d
     }
     if (tmp) {
         if (e != cudaSuccess) cudaStreamSynchronize(c->stream);
-        cudaFree(tmp);
+        lbm::dfree(tmp);
     }
     if (e != cudaSuccess) return cuda_fail(c, "lbm_macroscopic", e);
     return LBM_OK;
@@ -635,7 +823,7 @@ lbm_status lbm_get_f_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int
     cudaError_t e = lbm::launch_get_box(c, x0, y0, z0, bx, by, bz, tmp);
     if (e == cudaSuccess) e = cudaMemcpyAsync(out, tmp, (size_t)B * lbm::Q * sizeof(double), cudaMemcpyDeviceToHost, c->stream);
     cudaError_t e2 = cudaStreamSynchronize(c->stream);
-    cudaFree(tmp);
+    lbm::dfree(tmp);
     if (e == cudaSuccess) e = e2;
     if (e != cudaSuccess) return cuda_fail(c, "lbm_get_f_box", e);
     return LBM_OK;
@@ -656,7 +844,7 @@ lbm_status lbm_set_f(lbm_ctx* c, const double* f_dense) {
         cudaError_t e = cudaMemcpyAsync(tmp, f_dense, (size_t)N * lbm::Q * sizeof(double), cudaMemcpyHostToDevice, c->stream);
         if (e == cudaSuccess) e = lbm::launch_set_dense(c, tmp);
         cudaError_t e2 = cudaStreamSynchronize(c->stream);
-        cudaFree(tmp);
+        lbm::dfree(tmp);
         if (e == cudaSuccess) e = e2;
         if (e != cudaSuccess) return cuda_fail(c, "lbm_set_f", e);
     }
@@ -674,6 +862,7 @@ lbm_status lbm_adjoint(lbm_ctx* c, int T, int ckpt_every, int plane_x, double* l
     if (c->gen) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint supports only the quasi-compressible LBGK model");
     if (c->lid_face >= 0) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint does not support a moving wall");
     if (c->bc != LBM_BC_EQUILIBRIUM) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint supports only the equilibrium closures");
+    if (c->ghost_lo || c->ghost_hi) return fail(c, LBM_EUNSUPPORTED, "lbm_adjoint does not support slab contexts");
     if (c->n_tiles == 0) {
         *loss = 0.0;
         if (dL_dtau) *dL_dtau = 0.0;
@@ -703,7 +892,7 @@ lbm_status lbm_get_tiles(lbm_ctx* c, int32_t* tile_map, uint32_t* non_empty, int
 lbm_status lbm_get_info(lbm_ctx* c, int64_t* n_tiles, int64_t* n_nonsolid, int64_t* copy_bytes) {
     LBM_CHECK_CTX(c);
     if (n_tiles) *n_tiles = c->n_tiles;
-    if (n_nonsolid) *n_nonsolid = c->n_nonsolid;
+    if (n_nonsolid) *n_nonsolid = c->n_own_nonsolid;
     if (copy_bytes) *copy_bytes = c->n_tiles * lbm::Q * lbm::SLOTS * (int64_t)lbm::dtype_size(c->dtype);
     return LBM_OK;
 }
@@ -759,6 +948,28 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* blob, size_t nbytes) {
     if (c->seed) LBM_CUDA(c, cudaMemcpyAsync(c->seed + c->cur, &h.rng_step, 4, cudaMemcpyHostToDevice, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     c->state_set = true;
+    return LBM_OK;
+}
+
+// ---------------------------------------------------------------- test hooks
+int64_t lbm_testing_live_allocations(void) { return lbm::g_live_allocs.load(); }
+
+void lbm_testing_fail_allocation(int64_t k) { lbm::g_fail_after.store(k < 0 ? -1 : k); }
+
+int lbm_testing_checked_build(void) {
+#ifdef LBM_CHECKED
+    return 1;
+#else
+    return 0;
+#endif
+}
+
+lbm_status lbm_testing_plant_check(lbm_ctx* c, uint64_t word) {
+    LBM_CHECK_CTX(c);
+    if (!c->check) return fail(c, LBM_EUNSUPPORTED, "not a checked build (LBM_CHECKED)");
+    const unsigned long long w = word;
+    LBM_CUDA(c, cudaMemcpyAsync(c->check, &w, sizeof(w), cudaMemcpyHostToDevice, c->stream));
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     return LBM_OK;
 }
 

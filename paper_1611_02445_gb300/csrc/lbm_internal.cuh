@@ -145,6 +145,18 @@ struct StepParams {
     // LBM_BC_ZOU_HE with the box faces of the inlet and the outlet nodes
     int bc;
     int zh_face[2];
+    // extents the checked build (LBM_CHECKED) tests every index against, and its error
+    // word (NULL in the normal build): the first failed check stores (code << 56) | value
+    int64_t n_tiles, n_lanes, n_fill;
+    unsigned long long* check;
+};
+
+// Codes of the checked build's error word.
+enum : unsigned {
+    CHECK_HEADER = 1,      // a work-group header or fill range outside the context's arrays
+    CHECK_OWN_TILE = 2,    // a node word whose tile is not in its group
+    CHECK_NEIGHBOUR = 3,   // a pulled direction whose neighbour rank is not a kept tile
+    CHECK_FILL = 4         // a fill-list entry whose tile is not in its group
 };
 
 // A parameter in the arithmetic type R: the FP64 value or its FP32 copy.
@@ -165,7 +177,17 @@ struct lbm_ctx {
     int lid_face = -1;          // moving box face (lbm_set_lid), -1 for none
     int bc = 0;                 // inlet/outlet scheme (lbm_set_bc)
     uint32_t* seed = nullptr;   // step counters of the rounding hash, one per copy
+    unsigned long long* check = nullptr;   // error word of the checked build (LBM_CHECKED), else NULL
     int64_t n_tiles = 0, n_nonsolid = 0;
+    // Tiles the step updates, reduces and exports: ranks [own_k0, own_k1). All of them in
+    // a whole-domain context; a slab context (lbm_create_slab) also holds one ghost tile
+    // plane below and/or above its own planes (ranks [0, own_k0) and [own_k1, n_tiles)),
+    // which only receive the neighbours' boundary data.
+    int64_t own_k0 = 0, own_k1 = 0;
+    int ghost_lo = 0, ghost_hi = 0;     // ghost tile planes at the bottom / top of the box
+    int64_t bnd_lo = 0, bnd_hi = 0;     // kept tiles in the lowest / highest own tile plane
+    int z_plane0 = 0;                   // global tile plane of the box's first plane (slab)
+    int64_t n_own_nonsolid = 0;         // non-solid nodes of the own tiles
     cudaStream_t stream = nullptr;
     int32_t* tile_map = nullptr;
     uint32_t* non_empty = nullptr;
@@ -202,6 +224,12 @@ struct lbm_ctx {
 };
 
 namespace lbm {
+// Every device buffer of the library is allocated and released through these two
+// (lbm_capi.cu): they count live buffers, and the host-side test hook of lbm_testing.h
+// can make the k-th allocation fail as cudaMalloc does when memory runs out.
+cudaError_t dmalloc(void** p, size_t bytes);
+void dfree(void* p);
+
 // Launchers (defined in lbm_tiles.cu / lbm_step.cu); all queue work on ctx->stream and
 // return cudaGetLastError() of the launch.
 cudaError_t launch_tile_flags(const uint8_t* nt, int nx, int ny, int nz, int Tx, int Ty, int Tz,
@@ -218,6 +246,7 @@ cudaError_t prepare_step(lbm_ctx* c);
 cudaError_t launch_reduce(lbm_ctx* c, double* d_out);
 cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64);
 cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, int bz, double* d_out);
+cudaError_t launch_halo(lbm_ctx* c, int side, int pack, void* buf);
 cudaError_t launch_set_dense(lbm_ctx* c, const double* d_dense);
 cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense);
 cudaError_t launch_gfield_compact(lbm_ctx* c);

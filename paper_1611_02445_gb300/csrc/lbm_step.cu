@@ -85,6 +85,41 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
+// ------------------------------------------------------------------- checked build
+// With LBM_CHECKED every index the step takes from its tables is tested before use; a
+// failed test records (code << 56) | value in the context's error word (the first one
+// wins) and the access is skipped, so no out-of-range address is formed. Without it
+// check_ok is constant true and the tests compile away.
+__device__ __forceinline__ bool check_ok(bool ok, unsigned code, int64_t value, const StepParams& p) {
+#ifdef LBM_CHECKED
+    if (!ok && p.check)
+        atomicCAS(p.check, 0ull, ((unsigned long long)code << 56) | ((unsigned long long)value & 0x00ffffffffffffffull));
+    return ok;
+#else
+    (void)ok;
+    (void)code;
+    (void)value;
+    (void)p;
+    return true;
+#endif
+}
+
+// A work group's header as the stages use it: in the checked build a header outside
+// the context's arrays is recorded and replaced by an empty group.
+template <int DT>
+__device__ __forceinline__ int4 group_header(const int4 h, const StepParams& p) {
+    const bool ok = h.x >= 0 && h.y >= 0 && h.y <= StepCfg<DT>::MAX_TILES && (int64_t)h.x + h.y <= p.n_tiles &&
+                    h.z >= 0 && h.w >= 0 && h.w <= StepCfg<DT>::THREADS && (int64_t)h.z + h.w <= p.n_lanes;
+    return check_ok(ok, CHECK_HEADER, h.x, p) ? h : make_int4(0, 0, 0, 0);
+}
+// The same for a group's fill range, which only launches with fill stages (FL) load.
+template <bool FL>
+__device__ __forceinline__ int2 fill_range(const int2 fr, const StepParams& p) {
+    if constexpr (!FL) return make_int2(0, 0);
+    const bool ok = fr.x >= 0 && fr.y >= 0 && (int64_t)fr.x + fr.y <= p.n_fill;
+    return check_ok(ok, CHECK_HEADER, fr.x, p) ? fr : make_int2(0, 0);
+}
+
 // Staged element: the stored element for F64/F32; for F16S the aligned 32-bit word that
 // holds the wanted half (cp.async moves at least 4 bytes), with the half picked later.
 template <int DT> struct Staged { using E = uint32_t; };
@@ -143,12 +178,13 @@ __device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const in
 // the wanted half).
 template <int DT, int MODE>
 __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int dslot, const int4 h,
-                                             const typename Store<DT>::T* __restrict__ A) {
+                                             const typename Store<DT>::T* __restrict__ A, const StepParams& p) {
     using T = typename Store<DT>::T;
     const int t = threadIdx.x;
     const uint32_t w = sm.word[mslot][t];
     if (((w >> WORD_TYPE_SHIFT) & 3u) == LBM_SOLID) return;
     const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
+    if (!check_ok(lt < h.y, CHECK_OWN_TILE, (int64_t)h.z + t, p)) return;
     const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
     const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
 #pragma unroll
@@ -162,7 +198,9 @@ __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int ds
             const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
             const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
             const int ss = (sx & 3) | ((sy & 3) << 2) | ((sz & 3) << 4);
-            src = (int64_t)sm.nbr[mslot][lt][nb] * (Q * SLOTS) + i * SLOTS + ss;
+            const int32_t r = sm.nbr[mslot][lt][nb];
+            if (!check_ok(r >= 0 && r < p.n_tiles, CHECK_NEIGHBOUR, (int64_t)(h.x + lt) * NBR_STRIDE + nb, p)) continue;
+            src = (int64_t)r * (Q * SLOTS) + i * SLOTS + ss;
         }
         if (DT == LBM_F64) {
             cp_async8(&sm.data[dslot][i][t], A + src);
@@ -185,6 +223,35 @@ template <int MODE>
 __device__ __forceinline__ uint32_t upper_halves(int s, uint32_t w) {
     const uint32_t own = (s & 1) ? 0x7ffffu : 0u;
     return MODE == STEP_RW ? own : own ^ (CX_DIRS & ~w);
+}
+
+// FP16 store of a node's 19 results h (FP32, unscaled) that keeps the node's mass and
+// momentum: rounding each value to the nearest binary16 leaves residues r_i = h_i - stored_i
+// whose sums over the node (mass sum r_i, momentum sum c_i r_i) the collision cannot relax:
+// they persist from step to step like a small spurious source and force, while the
+// residues in the other moments decay. So the directions with c_x, c_y, c_z != 0 other
+// than 1 (E), 2 (N), 5 (T) are rounded first; E, N and T, each moving along one axis only,
+// then round h + (that axis' residue so far), and the rest population 0 last rounds
+// h + (the mass residue of all others). The node's stored mass and momentum then differ
+// from the computed ones by at most half a binary16 spacing of h_0, h_1, h_2, h_5.
+__device__ __forceinline__ void store_f16_conserving(const float v[Q], __half* __restrict__ dst) {
+    float rx = 0.f, ry = 0.f, rz = 0.f, m = 0.f;
+    auto put = [&](int i, float target) {
+        const __half q = __float2half_rn(target * F16_SCALE);
+        dst[i * SLOTS] = q;
+        const float r = v[i] - __half2float(q) * F16_INV_SCALE;
+        m += r;
+        if (cx(i)) rx += cx(i) > 0 ? r : -r;
+        if (cy(i)) ry += cy(i) > 0 ? r : -r;
+        if (cz(i)) rz += cz(i) > 0 ? r : -r;
+    };
+#pragma unroll
+    for (int i = 3; i < Q; i++)
+        if (i != 5) put(i, v[i]);
+    put(1, v[1] + rx);
+    put(2, v[2] + ry);
+    put(5, v[5] + rz);
+    put(0, v[0] + m);
 }
 
 template <int DT, bool VAR, int MODE, bool GEN>
@@ -239,6 +306,7 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     } else {
         collide<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
     }
+    if (!check_ok(lt < h.y, CHECK_OWN_TILE, (int64_t)h.z + t, p)) return;
     const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
     if constexpr (DT == LBM_F16S && VAR && MODE == STEP_FULL) {
         // stochastic rounding: two 16-bit dithers per hash of (key, node, pair)
@@ -249,6 +317,8 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
             B[own + i * SLOTS + s] = half_dithered(v[i] * F16_SCALE, r & 0xffffu);
             if (i + 1 < Q) B[own + (i + 1) * SLOTS + s] = half_dithered(v[i + 1] * F16_SCALE, r >> 16);
         }
+    } else if constexpr (DT == LBM_F16S && MODE == STEP_FULL) {
+        store_f16_conserving(v, B + own + s);
     } else {
 #pragma unroll
         for (int i = 0; i < Q; i++) B[own + i * SLOTS + s] = to_store<DT>(v[i], i);
@@ -262,13 +332,15 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
 // goes to thread THREADS - 1 - j, where the idle threads of a short group are; e0 is this
 // thread's first entry, staged in shared memory with the group's other metadata.
 template <int DT>
-__device__ __forceinline__ void fill_solid(typename Store<DT>::T* __restrict__ B, int t0, uint32_t e0,
-                                           const uint32_t* __restrict__ list, int nf) {
+__device__ __forceinline__ void fill_solid(typename Store<DT>::T* __restrict__ B, const int4 h, uint32_t e0,
+                                           const uint32_t* __restrict__ list, int nf, const StepParams& p) {
     using T = typename Store<DT>::T;
     const T nan = nan_value<DT>();
+    const int t0 = h.x;
     int j = StepCfg<DT>::THREADS - 1 - (int)threadIdx.x;
     for (uint32_t e = e0; j < nf; j += StepCfg<DT>::THREADS) {
         if (j >= StepCfg<DT>::THREADS) e = __ldg(list + j);
+        if (!check_ok((int)(e >> 6) < h.y, CHECK_FILL, e, p)) continue;
         T* q = B + (int64_t)(t0 + (int)(e >> 6)) * (Q * SLOTS) + (e & 63u);
 #pragma unroll
         for (int i = 0; i < Q; i++) q[i * SLOTS] = nan;
@@ -306,13 +378,16 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    issue_meta<DT, FL>(sm, 0, sm.hdr[0], sm.frng[0], nbr, fword, gfield_c, gfill);
+    issue_meta<DT, FL>(sm, 0, group_header<DT>(sm.hdr[0], p), fill_range<FL>(sm.frng[0], p), nbr, fword, gfield_c,
+                       gfill);
     cp_async_commit();
-    if (g0 + G < n_groups) issue_meta<DT, FL>(sm, 1, sm.hdr[1], sm.frng[1], nbr, fword, gfield_c, gfill);
+    if (g0 + G < n_groups)
+        issue_meta<DT, FL>(sm, 1, group_header<DT>(sm.hdr[1], p), fill_range<FL>(sm.frng[1], p), nbr, fword, gfield_c,
+                           gfill);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    issue_gather<DT, MODE>(sm, 0, 0, sm.hdr[0], A);
+    issue_gather<DT, MODE>(sm, 0, 0, group_header<DT>(sm.hdr[0], p), A, p);
     cp_async_commit();
     int it = 0;
     for (int64_t g = g0; g < n_groups; g += G, it++) {
@@ -322,17 +397,20 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         issue_hdr<FL>(&sm.hdr[(it + 3) & 3], &sm.frng[(it + 3) & 3], g + 3 * G, n_groups, groups, gfill_rng);
         cp_async_commit();
         if (g + 2 * G < n_groups)
-            issue_meta<DT, FL>(sm, (it + 2) % META_SLOTS, sm.hdr[(it + 2) & 3], sm.frng[(it + 2) & 3], nbr,
-                               fword, gfield_c, gfill);
+            issue_meta<DT, FL>(sm, (it + 2) % META_SLOTS, group_header<DT>(sm.hdr[(it + 2) & 3], p),
+                               fill_range<FL>(sm.frng[(it + 2) & 3], p), nbr, fword, gfield_c, gfill);
         cp_async_commit();
-        if (g + G < n_groups) issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, sm.hdr[(it + 1) & 3], A);
+        if (g + G < n_groups)
+            issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, group_header<DT>(sm.hdr[(it + 1) & 3], p),
+                                   A, p);
         cp_async_commit();
         // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
         cp_async_wait<3>();
-        compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, sm.hdr[it & 3], B, p, has_gf, key);
+        const int4 h = group_header<DT>(sm.hdr[it & 3], p);
+        compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, h, B, p, has_gf, key);
         if constexpr (FL) {
-            const int2 fr = sm.frng[it & 3];
-            fill_solid<DT>(B, sm.hdr[it & 3].x, sm.fill[it % META_SLOTS][threadIdx.x], gfill + fr.x, fr.y);
+            const int2 fr = fill_range<FL>(sm.frng[it & 3], p);
+            fill_solid<DT>(B, h, sm.fill[it % META_SLOTS][threadIdx.x], gfill + fr.x, fr.y, p);
         }
     }
     cp_async_wait<0>();

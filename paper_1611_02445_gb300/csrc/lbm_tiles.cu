@@ -306,20 +306,28 @@ template <int DT>
 __device__ __forceinline__ void node_moments(const typename Store<DT>::T* __restrict__ f, int64_t k, int s,
                                              double m[4]) {
     if constexpr (DT == LBM_F64) {
+        // exact fixed-point sums; the conversion maps NaN and Inf to finite integers, so
+        // a non-finite population is tested for on its exponent bits and makes every
+        // moment of the node NaN (what the mass watchdog of lbm_reduce looks for)
         int64_t r = 0, jx = 0, jy = 0, jz = 0;
+        uint64_t nonfinite = 0;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const int64_t q = fix_from_double(f[(k * Q + i) * SLOTS + s]);
+            const double v = f[(k * Q + i) * SLOTS + s];
+            const uint64_t b = (uint64_t)__double_as_longlong(v);
+            nonfinite |= (~b & 0x7ff0000000000000ull) == 0 ? 1ull : 0ull;
+            const int64_t q = fix_from_double(v);
             r += q;
             if (cx(i)) jx += cx(i) > 0 ? q : -q;
             if (cy(i)) jy += cy(i) > 0 ? q : -q;
             if (cz(i)) jz += cz(i) > 0 ? q : -q;
         }
         const double sc = 1.0 / (double)(1ull << FIX_SHIFT);
-        m[0] = __ll2double_rn(r) * sc;
-        m[1] = __ll2double_rn(jx) * sc;
-        m[2] = __ll2double_rn(jy) * sc;
-        m[3] = __ll2double_rn(jz) * sc;
+        const double nan = __longlong_as_double(0x7ff8000000000000ll);
+        m[0] = nonfinite ? nan : __ll2double_rn(r) * sc;
+        m[1] = nonfinite ? nan : __ll2double_rn(jx) * sc;
+        m[2] = nonfinite ? nan : __ll2double_rn(jy) * sc;
+        m[3] = nonfinite ? nan : __ll2double_rn(jz) * sc;
     } else {
         float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, er = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
 #pragma unroll
@@ -394,21 +402,38 @@ int reduce_blocks(int64_t n_tiles) {
     return (int)std::max<int64_t>(1, std::min<int64_t>((n_tiles * SLOTS + RED_THREADS - 1) / RED_THREADS, 152 * 4));
 }
 
+// The own tiles of a context (all of them, or a slab context's without its ghost planes)
+// as pointers to their first tile: populations, masks, tile indices and per-slot force.
+struct OwnTiles {
+    const void* f;
+    const uint64_t* smask;
+    const uint32_t* non_empty;
+    const void* gfield;
+    int64_t n;
+};
+static OwnTiles own_tiles(const lbm_ctx* c) {
+    const int64_t k0 = c->own_k0;
+    const size_t gsize = c->dtype == LBM_F64 ? 8 : 4;
+    return {static_cast<const char*>(c->f[c->cur]) + (size_t)k0 * Q * SLOTS * dtype_size(c->dtype), c->smask + k0,
+            c->non_empty + k0, c->gfield ? static_cast<const char*>(c->gfield) + (size_t)k0 * SLOTS * gsize : nullptr,
+            c->own_k1 - k0};
+}
+
 cudaError_t launch_reduce(lbm_ctx* c, double* d_out) {
     const int nb = c->n_partials;
-    const void* A = c->f[c->cur];
+    const OwnTiles o = own_tiles(c);
     switch (c->dtype) {
         case LBM_F64:
-            k_reduce<LBM_F64><<<nb, RED_THREADS, 0, c->stream>>>((const double*)A, c->smask, c->gfield,
-                                                                 c->n_tiles, c->p, c->partials);
+            k_reduce<LBM_F64><<<nb, RED_THREADS, 0, c->stream>>>((const double*)o.f, o.smask, o.gfield, o.n, c->p,
+                                                                 c->partials);
             break;
         case LBM_F32:
-            k_reduce<LBM_F32><<<nb, RED_THREADS, 0, c->stream>>>((const float*)A, c->smask, c->gfield,
-                                                                 c->n_tiles, c->p, c->partials);
+            k_reduce<LBM_F32><<<nb, RED_THREADS, 0, c->stream>>>((const float*)o.f, o.smask, o.gfield, o.n, c->p,
+                                                                 c->partials);
             break;
         default:
-            k_reduce<LBM_F16S><<<nb, RED_THREADS, 0, c->stream>>>((const __half*)A, c->smask, c->gfield,
-                                                                  c->n_tiles, c->p, c->partials);
+            k_reduce<LBM_F16S><<<nb, RED_THREADS, 0, c->stream>>>((const __half*)o.f, o.smask, o.gfield, o.n, c->p,
+                                                                  c->partials);
     }
     k_reduce_final<<<1, RED_THREADS, 0, c->stream>>>(c->partials, nb, d_out);
     return cudaGetLastError();
@@ -454,11 +479,12 @@ __global__ void k_macro(const typename Store<DT>::T* __restrict__ f, const uint6
 }
 
 template <typename O>
-static void macro_dispatch(lbm_ctx* c, const void* A, O* rho, O* u) {
-    const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
-#define LBM_MACRO(DT, TT)                                                                               \
-    k_macro<DT, O><<<g, 256, 0, c->stream>>>((const TT*)A, c->smask, c->non_empty, c->gfield, c->n_tiles, \
-                                             c->nx, c->ny, c->nz, c->Tx, c->Ty, c->p, rho, u)
+static void macro_dispatch(lbm_ctx* c, O* rho, O* u) {
+    const OwnTiles o = own_tiles(c);
+    const unsigned g = grid_for(o.n * SLOTS, 256);
+#define LBM_MACRO(DT, TT)                                                                                 \
+    k_macro<DT, O><<<g, 256, 0, c->stream>>>((const TT*)o.f, o.smask, o.non_empty, o.gfield, o.n, c->nx, c->ny, \
+                                             c->nz, c->Tx, c->Ty, c->p, rho, u)
     if (c->dtype == LBM_F64) LBM_MACRO(LBM_F64, double);
     else if (c->dtype == LBM_F32) LBM_MACRO(LBM_F32, float);
     else LBM_MACRO(LBM_F16S, __half);
@@ -466,9 +492,9 @@ static void macro_dispatch(lbm_ctx* c, const void* A, O* rho, O* u) {
 }
 
 cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64) {
-    if (c->n_tiles == 0) return cudaSuccess;
-    if (out_f64) macro_dispatch<double>(c, c->f[c->cur], (double*)rho, (double*)u);
-    else macro_dispatch<float>(c, c->f[c->cur], (float*)rho, (float*)u);
+    if (c->own_k1 <= c->own_k0) return cudaSuccess;
+    if (out_f64) macro_dispatch<double>(c, (double*)rho, (double*)u);
+    else macro_dispatch<float>(c, (float*)rho, (float*)u);
     return cudaGetLastError();
 }
 
@@ -584,13 +610,13 @@ __global__ void k_gfield_compact(G* __restrict__ gc, const G* __restrict__ gt, c
 }
 
 cudaError_t launch_gfield_compact(lbm_ctx* c) {
-    const unsigned g = grid_for(c->n_nonsolid, 256);
+    const unsigned g = grid_for(c->n_own_nonsolid, 256);
     if (c->dtype == LBM_F64)
         k_gfield_compact<double><<<g, 256, 0, c->stream>>>((double*)c->gfield_c, (const double*)c->gfield, c->fidx,
-                                                           c->n_nonsolid);
+                                                           c->n_own_nonsolid);
     else
         k_gfield_compact<float><<<g, 256, 0, c->stream>>>((float*)c->gfield_c, (const float*)c->gfield, c->fidx,
-                                                          c->n_nonsolid);
+                                                          c->n_own_nonsolid);
     return cudaGetLastError();
 }
 
@@ -619,8 +645,9 @@ __global__ void k_mark_lid(uint32_t* __restrict__ fword, const uint32_t* __restr
 }
 
 cudaError_t launch_mark_lid(lbm_ctx* c, int face) {
-    if (c->n_nonsolid == 0) return cudaSuccess;
-    k_mark_lid<<<grid_for(c->n_nonsolid, 256), 256, 0, c->stream>>>(c->fword, c->fidx, c->non_empty, c->n_nonsolid,
+    if (c->n_own_nonsolid == 0) return cudaSuccess;
+    k_mark_lid<<<grid_for(c->n_own_nonsolid, 256), 256, 0, c->stream>>>(c->fword, c->fidx, c->non_empty,
+                                                                       c->n_own_nonsolid,
                                                                    c->Tx, c->Ty, c->nx, c->ny, c->nz, face);
     return cudaGetLastError();
 }
@@ -634,6 +661,46 @@ cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense) {
         k_gfield<float><<<g, 256, 0, c->stream>>>((float*)c->gfield, d_dense, c->non_empty, c->n_tiles, c->nx,
                                                   c->ny, c->nz, c->Tx, c->Ty);
     return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------------
+// Halo of a slab context (lbm_create_slab): the populations that cross the cut between
+// two slabs. A node of the lowest own plane pulls from the plane below through the five
+// directions with c_z = +1, one of the highest own plane from the plane above through
+// the five with c_z = -1. Pack copies the own boundary plane's blocks of the directions
+// its neighbour reads (side 0: the lowest plane, for the slab below, c_z = -1; side 1:
+// the highest, for the slab above, c_z = +1) from the current copy into buf, laid out
+// [direction][tile][64]; unpack copies buf into the ghost plane on that side (side 0:
+// c_z = +1, side 1: c_z = -1). Both are strided device copies of whole 64-value blocks.
+cudaError_t launch_halo(lbm_ctx* c, int side, int pack, void* buf) {
+    static const int kDown[5] = {6, 12, 14, 16, 18};   // c_z = -1
+    static const int kUp[5] = {5, 11, 13, 15, 17};     // c_z = +1
+    const size_t es = dtype_size(c->dtype);
+    const size_t block = SLOTS * es, pitch = (size_t)Q * SLOTS * es;
+    int64_t k0, n;
+    const int* dirs;
+    if (pack) {
+        k0 = side == 0 ? c->own_k0 : c->own_k1 - c->bnd_hi;
+        n = side == 0 ? c->bnd_lo : c->bnd_hi;
+        dirs = side == 0 ? kDown : kUp;
+    } else {
+        k0 = side == 0 ? 0 : c->own_k1;
+        n = side == 0 ? c->own_k0 : c->n_tiles - c->own_k1;
+        dirs = side == 0 ? kUp : kDown;
+    }
+    if (n == 0) return cudaSuccess;
+    char* f = static_cast<char*>(c->f[c->cur]) + (size_t)k0 * pitch;
+    char* b = static_cast<char*>(buf);
+    for (int d = 0; d < 5; d++) {
+        char* tiles = f + (size_t)dirs[d] * block;
+        char* part = b + (size_t)d * n * block;
+        const cudaError_t e = pack ? cudaMemcpy2DAsync(part, block, tiles, pitch, block, (size_t)n,
+                                                       cudaMemcpyDeviceToDevice, c->stream)
+                                   : cudaMemcpy2DAsync(tiles, pitch, part, block, block, (size_t)n,
+                                                       cudaMemcpyDeviceToDevice, c->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace lbm

@@ -23,6 +23,7 @@ PERIODIC_X, PERIODIC_Y, PERIODIC_Z = 1, 2, 4
 STATUS = {0: "LBM_OK", 1: "LBM_EINVAL", 2: "LBM_ENOMEM", 3: "LBM_ECUDA", 4: "LBM_EUNSUPPORTED",
           5: "LBM_ESTATE", 6: "LBM_ENONFINITE", 7: "LBM_ETIMEOUT", 8: "LBM_EINTERNAL"}
 HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "lbm.h")
+TESTING_HEADER = os.path.join(os.path.dirname(HEADER), "lbm_testing.h")
 
 
 class LBMError(RuntimeError):
@@ -35,7 +36,9 @@ _lib = None
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the normal build, or the checked build
+    (LBM_CHECKED, see include/lbm_testing.h) when the environment sets LBM_CHECKED=1."""
+    return _build.LIB_CHECKED if os.environ.get("LBM_CHECKED") == "1" else _build.LIB
 
 
 def load():
@@ -74,16 +77,29 @@ def load():
     L.lbm_load_state.argtypes = [vp, vp, ct.c_size_t]
     L.lbm_adjoint.argtypes = [vp, i, i, i, pd, vp, i, pd]
     L.lbm_build_tiles_noalloc.argtypes = [vp, i, i, i, vp, vp, ct.POINTER(i64), vp]
-    for name in header_functions():
+    pi = ct.POINTER(ct.c_int)
+    L.lbm_partition_z.argtypes = [vp, i, i, i, i, pi]
+    L.lbm_slab_geometry.argtypes = [vp, i, i, i, u, i, i, vp, pi, pi, pi]
+    L.lbm_create_slab.argtypes = [vp, i, i, i, i, i, u, i, i, vp, ct.POINTER(vp)]
+    L.lbm_halo_bytes.argtypes = [vp, i, i, ct.POINTER(ct.c_size_t)]
+    L.lbm_halo_pack.argtypes = [vp, i, vp]
+    L.lbm_halo_unpack.argtypes = [vp, i, vp]
+    L.lbm_testing_live_allocations.argtypes = []
+    L.lbm_testing_live_allocations.restype = i64
+    L.lbm_testing_fail_allocation.argtypes = [i64]
+    L.lbm_testing_fail_allocation.restype = None
+    L.lbm_testing_checked_build.argtypes = []
+    L.lbm_testing_plant_check.argtypes = [vp, ct.c_uint64]
+    for name in header_functions() + header_functions(TESTING_HEADER):
         getattr(L, name)   # every declared entry point must be exported
     _lib = L
     return L
 
 
-def header_functions():
-    """Names of the functions declared in include/lbm.h."""
-    text = open(HEADER).read()
-    return re.findall(r"^\s*(?:lbm_status|void|const char\s*\*)\s*\**\s*(lbm_\w+)\s*\(", text, re.M)
+def header_functions(header: str = HEADER):
+    """Names of the functions declared in include/lbm.h (or another of the headers)."""
+    text = open(header).read()
+    return re.findall(r"^\s*(?:lbm_status|void|int|int64_t|const char\s*\*)\s*\**\s*(lbm_\w+)\s*\(", text, re.M)
 
 
 def _ptr(x):
@@ -312,6 +328,79 @@ def lbm_build_tiles_noalloc(node_type, nx, ny, nz, tile_map, non_empty, stream=N
                    "use lbm_create", 1: "invalid arguments or node types outside 0..3"}.get(st, "")
         raise LBMError(st, f"lbm_build_tiles_noalloc: {hint}")
     return n.value
+
+
+# ------------------------------------------------------------ slabs and their halos
+def lbm_partition_z(node_type, nranks: int) -> np.ndarray:
+    """Tile-plane bounds of nranks z-slabs with about equal non-solid node counts (host)."""
+    nt = np.ascontiguousarray(node_type, dtype=np.uint8)
+    nz, ny, nx = nt.shape
+    out = (ct.c_int * (nranks + 1))()
+    st = load().lbm_partition_z(nt.ctypes.data, nx, ny, nz, int(nranks), out)
+    if st != 0:
+        raise LBMError(st, load().lbm_last_error(None).decode())
+    return np.array(out[:], dtype=np.int64)
+
+
+def lbm_slab_geometry(node_type, periodic: int, plane_begin: int, plane_end: int):
+    """The node types of a slab's box and its ghost planes (host): (sub, ghost_lo, ghost_hi)."""
+    nt = np.ascontiguousarray(node_type, dtype=np.uint8)
+    nz, ny, nx = nt.shape
+    nzs, gl, gh = ct.c_int(), ct.c_int(), ct.c_int()
+    L = load()
+    st = L.lbm_slab_geometry(nt.ctypes.data, nx, ny, nz, int(periodic), int(plane_begin), int(plane_end), None,
+                             ct.byref(nzs), ct.byref(gl), ct.byref(gh))
+    if st != 0:
+        raise LBMError(st, L.lbm_last_error(None).decode())
+    sub = np.empty((nzs.value, ny, nx), np.uint8)
+    L.lbm_slab_geometry(nt.ctypes.data, nx, ny, nz, int(periodic), int(plane_begin), int(plane_end),
+                        sub.ctypes.data, ct.byref(nzs), ct.byref(gl), ct.byref(gh))
+    return sub, gl.value, gh.value
+
+
+def lbm_create_slab(node_type, dtype, periodic, plane_begin, plane_end, stream=None):
+    nt = np.ascontiguousarray(node_type, dtype=np.uint8)
+    nz, ny, nx = nt.shape
+    out = ct.c_void_p()
+    L = load()
+    st = L.lbm_create_slab(nt.ctypes.data, nx, ny, nz, 4, int(dtype), int(periodic), int(plane_begin),
+                           int(plane_end), _stream(stream), ct.byref(out))
+    if st != 0:
+        raise LBMError(st, L.lbm_last_error(None).decode())
+    return out.value
+
+
+def lbm_halo_bytes(ctx, side: int, pack: bool) -> int:
+    n = ct.c_size_t()
+    _check(load().lbm_halo_bytes(ctx, int(side), int(bool(pack)), ct.byref(n)), ctx)
+    return n.value
+
+
+def lbm_halo_pack(ctx, side: int, buf):
+    _check(load().lbm_halo_pack(ctx, int(side), _ptr(buf)), ctx)
+
+
+def lbm_halo_unpack(ctx, side: int, buf):
+    _check(load().lbm_halo_unpack(ctx, int(side), _ptr(buf)), ctx)
+
+
+# ------------------------------------------------------------------ test hooks
+def testing_live_allocations() -> int:
+    """Device buffers the library holds now (include/lbm_testing.h)."""
+    return int(load().lbm_testing_live_allocations())
+
+
+def testing_fail_allocation(k: int):
+    """Make the k-th device allocation from now on fail as out of memory (k < 0: none)."""
+    load().lbm_testing_fail_allocation(int(k))
+
+
+def testing_checked_build() -> bool:
+    return bool(load().lbm_testing_checked_build())
+
+
+def testing_plant_check(ctx, word: int):
+    _check(load().lbm_testing_plant_check(ctx, int(word)), ctx)
 
 
 # ------------------------------------------------------------------ convenience class

@@ -27,8 +27,37 @@ def test_header_declares_the_boundary():
 
 def test_every_declared_symbol_is_exported(L):
     raw = ct.CDLL(lbm.library_path())
-    for n in lbm.header_functions():
+    for n in lbm.header_functions() + lbm.header_functions(lbm.TESTING_HEADER):
         assert hasattr(raw, n), n
+
+
+def test_checked_library_builds_and_exports_the_same_symbols():
+    path = B.build(checked=True)
+    raw = ct.CDLL(path)
+    for n in lbm.header_functions() + lbm.header_functions(lbm.TESTING_HEADER):
+        assert hasattr(raw, n), n
+    raw.lbm_testing_checked_build.restype = ct.c_int
+    assert raw.lbm_testing_checked_build() == 1
+    assert L_checked_flag(lbm.load()) == 0
+
+
+def L_checked_flag(L):
+    return int(L.lbm_testing_checked_build())
+
+
+def test_injected_allocation_failure_reports_enomem_and_leaks_nothing(L):
+    """The host-side hook fails the next device allocation the way cudaMalloc does when
+    memory runs out: lbm_create releases what it holds and returns LBM_ENOMEM."""
+    nt = np.ones((8, 8, 8), np.uint8)
+    live = lbm.testing_live_allocations()
+    lbm.testing_fail_allocation(0)
+    try:
+        st, ctx = _create(L, nt, (8, 8, 8))
+    finally:
+        lbm.testing_fail_allocation(-1)
+    assert st == 2 and ctx is None                            # LBM_ENOMEM, no context
+    assert "memory" in L.lbm_last_error(None).decode()
+    assert lbm.testing_live_allocations() == live
 
 
 def test_build_targets_sm_103a_only():

@@ -22,9 +22,12 @@ Bars, per population, relative to the lattice weight w_i:
     nodes: 4e-6 (the bar of the small-box Zou-He tests). The completion forms rho and
     the unknown populations from sums of known ones, terms of order 1 in f, so its
     roundings are ~1e-7 absolute, a few 1e-6 of the diagonal weight 1/36;
-  - FP16 storage: the rounding of the stored value itself, k spacings of binary16 at
-    h_oracle * 2^12 (k = 1/2 round-to-nearest, 1 stochastic rounding, which picks either
-    neighbour), plus the FP32 arithmetic bound above;
+  - FP16 storage: the rounding of the stored value itself, in spacings of binary16 at
+    h_oracle * 2^12: stochastic rounding, which picks either neighbour, one spacing;
+    round-to-nearest half a spacing, except that the rounding carries the node's mass
+    and momentum residues into directions 1, 2, 5 (each takes its axis' residue: at most
+    the sum S of all 19 half spacings) and 0 (the mass residue: at most 3 S); plus the
+    FP32 arithmetic bound above;
   - the calibration kernels (propagation only, read/write only): bit for bit.
 """
 import numpy as np
@@ -90,8 +93,15 @@ def _check(dtype, Bg, Bo, f32_tol=F32_TOL):
         worst = float((err / w).max())
         assert worst <= f32_tol, worst
     else:
-        k = 2.0 if dtype == "f16sr" else 1.0          # one spacing (SR) or half of one (RN)
-        bound = k * _f16_bound(Bo, w) + F32_TOL * w
+        half = _f16_bound(Bo, w)
+        if dtype == "f16sr":
+            bound = 2.0 * half                        # one spacing: either neighbour
+        else:
+            S = half.sum(axis=0)                      # per node: all 19 half spacings
+            bound = half.copy()
+            bound[[1, 2, 5]] += S
+            bound[0] += 3.0 * S
+        bound = bound + F32_TOL * w
         worst = float((err / bound).max())
         assert worst <= 1.0, worst
     return worst

@@ -34,10 +34,13 @@ def _built():
 def test_stochastic_rounding_keeps_sub_spacing_increments():
     """16^3 periodic fluid box at rest, g_x = 1e-11, tau 0.8: the first post-collision h_1
     is about 1.7e-12, 6.8e-9 after the 2^12 scale, below half the smallest binary16
-    spacing (2^-25 = 3.0e-8), so round-to-nearest stores 0 everywhere, every step. Under
-    stochastic rounding the momentum after n steps is N g (n - 1/2) in expectation; the
-    noise of one step is about sqrt(10 N) * 2^-24 / 2^12 * 0.5 ~ 4.6e-10, so after 64
-    steps its standard deviation is ~3.7e-9 against 2.6e-6 expected (0.15 %)."""
+    spacing (2^-25 = 3.0e-8), so plain round-to-nearest would store 0 everywhere, every
+    step. Under stochastic rounding the momentum after n steps is N g (n - 1/2) in
+    expectation; the noise of one step is about sqrt(10 N) * 2^-24 / 2^12 * 0.5 ~ 4.6e-10,
+    so after 64 steps its standard deviation is ~3.7e-9 against 2.6e-6 expected (0.15 %).
+    The round-to-nearest store carries each node's momentum residue into one population
+    per axis, which can keep part of the increments but never more than they add up to:
+    its momentum stays between the rest value -N g / 2 and the expectation."""
     nt = I.dense_box(16, 16, 16)
     N = nt.size
     g, n = 1e-11, 64
@@ -47,14 +50,12 @@ def test_stochastic_rounding_keeps_sub_spacing_increments():
             L.set_params(0.8, (g, 0.0, 0.0))
             L.init_equilibrium()
             L.step(n)
-            out[dtype] = (L.reduce(), L.get_f())
-    (m_rn, p_rn), f_rn = out["f16s"]
-    _, W, _ = O.lattice()
-    assert np.array_equal(f_rn, np.broadcast_to(W[:, None, None, None], f_rn.shape))
-    assert p_rn[0] == pytest.approx(-0.5 * N * g, rel=1e-12)
-    (m_sr, p_sr), _ = out["f16sr"]
+            out[dtype] = L.reduce()
     expected = N * g * (n - 0.5)
+    m_rn, p_rn = out["f16s"]
+    m_sr, p_sr = out["f16sr"]
     print(f"momentum after {n} steps: RN {p_rn[0]:.4e}, SR {p_sr[0]:.4e}, expected {expected:.4e}")
+    assert -0.5 * N * g * (1 + 1e-9) <= p_rn[0] <= expected * (1 + 1e-9)
     assert abs(p_sr[0] - expected) <= 0.02 * expected
     assert abs(p_sr[1]) <= 0.02 * expected and abs(p_sr[2]) <= 0.02 * expected
 
@@ -136,8 +137,13 @@ def test_poiseuille_steady_state_per_format():
 
 # Bounds on a 64^3 periodic sphere pack (radius 8, porosity 0.35, the precision-sweep
 # recipe at a size the oracle runs in seconds) after 1000 steps against the oracle:
-# max |u - u_oracle| / u_max and the relative L2 error.
-CROP_BOUNDS = {"f64": (1e-9, 1e-10), "f32": (1e-5, 5e-6), "f16s": (5e-3, 1e-3), "f16sr": (5e-3, 1e-3)}
+# max |u - u_oracle| / u_max and the relative L2 error. FP32 and FP16 (round to nearest,
+# carrying each node's mass and momentum residue) are held to the velocity gates of the
+# precision targets, 1e-5 and 1e-3 of u_max, in both norms (measured: FP32 1.0e-6 /
+# 5.2e-7, FP16 5.0e-4 / 2.7e-4). Stochastic rounding meets the 1e-3 gate in the L2 norm
+# only: its max-norm bound, 2e-3, lies ABOVE the gate (measured 1.4e-3; the dither is
+# unbiased but adds noise of up to one binary16 spacing per store).
+CROP_BOUNDS = {"f64": (1e-9, 1e-10), "f32": (1e-5, 1e-5), "f16s": (1e-3, 1e-3), "f16sr": (2e-3, 1e-3)}
 
 
 def test_porous_crop_per_format_vs_oracle():
