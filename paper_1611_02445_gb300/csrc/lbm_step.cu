@@ -226,14 +226,16 @@ __device__ __forceinline__ uint32_t upper_halves(int s, uint32_t w) {
 }
 
 // FP16 store of a node's 19 results h (FP32, unscaled) that keeps the node's mass and
-// momentum: rounding each value to the nearest binary16 leaves residues r_i = h_i - stored_i
-// whose sums over the node (mass sum r_i, momentum sum c_i r_i) the collision cannot relax:
-// they persist from step to step like a small spurious source and force, while the
-// residues in the other moments decay. So the directions with c_x, c_y, c_z != 0 other
-// than 1 (E), 2 (N), 5 (T) are rounded first; E, N and T, each moving along one axis only,
-// then round h + (that axis' residue so far), and the rest population 0 last rounds
-// h + (the mass residue of all others). The node's stored mass and momentum then differ
-// from the computed ones by at most half a binary16 spacing of h_0, h_1, h_2, h_5.
+// momentum. Rounding each value to the nearest binary16 leaves residues
+// r_i = h_i - stored_i. Their sums over the node (mass sum r_i, momentum sum c_i r_i) are
+// what the collision cannot relax: they persist from step to step like a small spurious
+// source and force, while residues in the other moments decay. So the twelve diagonal
+// directions are rounded first. Each axis' momentum residue r is then carried into that
+// axis' two directions, +r/2 into the one along the axis and -r/2 into the opposite
+// one, which adds r to the momentum and nothing to the mass or the momentum flux. The
+// rest population 0, last, takes the mass residue. The stored node's momentum then
+// differs from the computed one by at most one binary16 spacing of its axis
+// populations per axis, and its mass by half a spacing of h_0.
 __device__ __forceinline__ void store_f16_conserving(const float v[Q], __half* __restrict__ dst) {
     float rx = 0.f, ry = 0.f, rz = 0.f, m = 0.f;
     auto put = [&](int i, float target) {
@@ -246,11 +248,14 @@ __device__ __forceinline__ void store_f16_conserving(const float v[Q], __half* _
         if (cz(i)) rz += cz(i) > 0 ? r : -r;
     };
 #pragma unroll
-    for (int i = 3; i < Q; i++)
-        if (i != 5) put(i, v[i]);
-    put(1, v[1] + rx);
-    put(2, v[2] + ry);
-    put(5, v[5] + rz);
+    for (int i = 7; i < Q; i++) put(i, v[i]);
+    const float hx = 0.5f * rx, hy = 0.5f * ry, hz = 0.5f * rz;
+    put(1, v[1] + hx);
+    put(3, v[3] - hx);
+    put(2, v[2] + hy);
+    put(4, v[4] - hy);
+    put(5, v[5] + hz);
+    put(6, v[6] - hz);
     put(0, v[0] + m);
 }
 

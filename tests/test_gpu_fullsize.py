@@ -25,9 +25,9 @@ Bars, per population, relative to the lattice weight w_i:
   - FP16 storage: the rounding of the stored value itself, in spacings of binary16 at
     h_oracle * 2^12: stochastic rounding, which picks either neighbour, one spacing;
     round-to-nearest half a spacing, except that the rounding carries the node's mass
-    and momentum residues into directions 1, 2, 5 (each takes its axis' residue: at most
-    the sum S of all 19 half spacings) and 0 (the mass residue: at most 3 S); plus the
-    FP32 arithmetic bound above;
+    and momentum residues into directions 1-6 (each takes half its axis' residue: at most
+    S / 2, S the sum of all 19 half spacings) and 0 (the mass residue: at most 2 S); plus
+    the FP32 arithmetic bound above;
   - the calibration kernels (propagation only, read/write only): bit for bit.
 """
 import numpy as np
@@ -99,8 +99,8 @@ def _check(dtype, Bg, Bo, f32_tol=F32_TOL):
         else:
             S = half.sum(axis=0)                      # per node: all 19 half spacings
             bound = half.copy()
-            bound[[1, 2, 5]] += S
-            bound[0] += 3.0 * S
+            bound[1:7] += 0.5 * S                     # half an axis' residue each
+            bound[0] += 2.0 * S                       # the mass residue
         bound = bound + F32_TOL * w
         worst = float((err / bound).max())
         assert worst <= 1.0, worst
