@@ -97,16 +97,24 @@ LBM_DF_HD DFConst make_df_const(double omega, double beta, double Fx, double Fy,
     return c;
 }
 
+// Directions whose fixed-point conversion runs on the FP64 pipe (fix_from_double_cvt);
+// the others use the integer-only fix_from_double. The split balances the FP64 pipe
+// against instruction issue.
+constexpr uint32_t FIX_CVT_DIRS = 0x7fu;
+
 // One direction pair (a with velocity c, b with -c) of weight class k, with
 //   cj = c.j', g9 = 9 beta c.F, g3 = 3 beta w c.F, winv = w / rho:
 //   Ye = A + winv (cj (4.5 omega cj + g9) - P),   Yo = 3 omega w cj + g3.
+// The even part dominates: |omega w rho| >= |w T / rho| and |Ye| >= |Yo| hold while
+// |c.u| < 1/3 (T <= 9 omega j^2, Yo ~ 3 omega w rho c.u), far inside the low-Mach range
+// of the method, so those three sums use FastTwoSum.
 LBM_DF_HD void df_pair(double& a, double& b, const DFConst& K, int k, dfl cj, dfl g9, dfl g3, dfl winv, dfl A,
                        dfl P) {
     const dfl T = df_sub(df_mul(cj, df_add(df_mul(K.om45, cj), g9)), P);
-    const dfl Ye = df_add(A, df_mul(winv, T));
+    const dfl Ye = df_add_dom(A, df_mul(winv, T));
     const dfl Yo = df_add(df_mul(K.ow3[k], cj), g3);
-    const double yp = df_to_double_pos(df_add(Ye, Yo));
-    const double ym = df_to_double_pos(df_sub(Ye, Yo));
+    const double yp = df_to_double_pos(df_add_dom(Ye, Yo));
+    const double ym = df_to_double_pos(df_sub_dom(Ye, Yo));
 #if defined(__CUDA_ARCH__)
     a = __fma_rn(K.om1, a, yp);
     b = __fma_rn(K.om1, b, ym);
@@ -124,7 +132,7 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool unifor
     // opposite directions (the FP64 pipe is kept for the final update)
     int64_t q[19];
 #pragma unroll
-    for (int i = 0; i < 19; i++) q[i] = fix_from_double(f[i]);
+    for (int i = 0; i < 19; i++) q[i] = (FIX_CVT_DIRS >> i) & 1u ? fix_from_double_cvt(f[i]) : fix_from_double(f[i]);
     const int64_t s13 = q[1] + q[3], s24 = q[2] + q[4], s56 = q[5] + q[6], s79 = q[7] + q[9], s810 = q[8] + q[10];
     const int64_t s1114 = q[11] + q[14], s1213 = q[12] + q[13], s1518 = q[15] + q[18], s1617 = q[16] + q[17];
     const int64_t d13 = q[1] - q[3], d24 = q[2] - q[4], d56 = q[5] - q[6], d79 = q[7] - q[9], d810 = q[8] - q[10];
@@ -159,7 +167,7 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool unifor
     A[1] = df_from_double(K.ow_d[1] * rho_i);
     A[2] = df_scale2(A[1], 0.5f);
     // rest population: Y0 = A0 - (w0 / rho) P
-    const dfl Y0 = df_sub(A[0], df_mul(df_mul(K.w0, inv), P));
+    const dfl Y0 = df_sub_dom(A[0], df_mul(df_mul(K.w0, inv), P));   // |A0| dominates while |u|^2 < 2/3
 #if defined(__CUDA_ARCH__)
     f[0] = __fma_rn(K.om1, f[0], df_to_double_pos(Y0));
 #else

@@ -31,6 +31,17 @@ int main() {
     }
     std::printf("fix_mismatches %ld\n", fix_bad);
 
+    // fix_from_double_cvt: d 2^58 rounded to nearest, ties to even, including ties
+    long cvt_bad = 0;
+    for (int n = 0; n < 2000000; n++) {
+        double d = std::ldexp(1.0 + U(rng), -(int)(rng() % 30)) * ((rng() & 1) ? -1.0 : 1.0);
+        if (n % 4 == 0) d = std::ldexp(std::floor(std::ldexp(d, 58)) + 0.5, -58);   // an exact tie
+        const LD ref = nearbyintl((LD)d * 0x1p58L);                                     // ties to even
+        if ((LD)fix_from_double_cvt(d) != ref) cvt_bad++;
+    }
+    if (fix_from_double_cvt(0.0) != 0 || fix_from_double_cvt(-0.0) != 0 || fix_from_double_cvt(1e-310) != 0) cvt_bad++;
+    std::printf("fix_cvt_mismatches %ld\n", cvt_bad);
+
     // df_from_fix: relative error of hi + lo against x 2^-58
     double fix_rel = 0;
     for (int n = 0; n < 2000000; n++) {

@@ -1,7 +1,9 @@
 """The FP64 step's hybrid arithmetic, built for the host from the same header the CUDA
 kernel compiles (lbm_df.cuh, lbm_collide_df.cuh), against long-double references:
 
-- the exact 64-bit fixed-point conversion of a double (2^-58 units, round half away);
+- the exact 64-bit fixed-point conversion of a double (2^-58 units, round half away), and
+  the one that scales through the exponent field and rounds on the FP64 pipe (ties to
+  even), ties included;
 - the fixed-point and FP64 to double-float conversions (relative error below 2^-47);
 - the double-float to double conversion (the nearest double, every case);
 - the LBGK + Guo collision of Eq. 2, 3, 7 (agreement with long double per population,
@@ -30,6 +32,10 @@ def measured(tmp_path_factory):
 
 def test_fixed_point_conversion_is_exact(measured):
     assert measured["fix_mismatches"] == 0
+
+
+def test_fixed_point_conversion_on_the_fp64_pipe_rounds_to_nearest_even(measured):
+    assert measured["fix_cvt_mismatches"] == 0
 
 
 def test_pair_conversions_within_2_pow_minus_47(measured):
