@@ -707,10 +707,10 @@ FP64_FLOPS_PER_NODE = 331
 # ncu capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean of
 # two launches after three warm-up steps), with the hash (step_source_hash) of the library
 # sources they were captured with; the bench reports them only while the sources match.
-TRAFFIC_PER_LAUNCH_256 = {"sources": "",
-                          "f64": 1989303168 + 1107922432,
-                          "f32": 855424256 + 578127104,
-                          "f16s": 822345472 + 329302144}
+TRAFFIC_PER_LAUNCH_256 = {"sources": "4989e4c9e635af67",
+                          "f64": 1970679040 + 1108261760,
+                          "f32": 856056832 + 578375296,
+                          "f16s": 824360960 + 329868416}
 
 if __name__ == "__main__":
     main()
