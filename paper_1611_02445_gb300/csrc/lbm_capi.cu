@@ -386,12 +386,16 @@ static lbm_status create_impl(const uint8_t* node_type, int on_device, int nx, i
     c->n_nonsolid = (int64_t)nonsolid;
     {
         // Work units of the step kernel: consecutive tiles, at most GROUP_MAX_TILES_* of
-        // them and at most GROUP_MAX_NODES (FP64: GROUP_MAX_NODES_F64) non-solid nodes, so that threads map to
-        // non-solid nodes only. Built once on the host from the per-node words.
-        std::vector<uint32_t> words((size_t)count * lbm::SLOTS);
+        // them and at most GROUP_MAX_NODES (FP64: GROUP_MAX_NODES_F64) non-solid nodes, so
+        // that threads map to non-solid nodes only. The host forms the groups greedily from
+        // the tiles' node counts (their solid masks: 8 bytes per tile) and decides per tile
+        // where its lanes and fill entries start; k_lane_lists then writes the per-lane
+        // lists on the device.
+        std::vector<uint64_t> smask_h((size_t)count);
         std::vector<uint32_t> tiles_h((size_t)count);
         if (count > 0) {
-            LBM_CREATE_CUDA(cudaMemcpyAsync(words.data(), c->nword, words.size() * 4, cudaMemcpyDeviceToHost, c->stream));
+            LBM_CREATE_CUDA(cudaMemcpyAsync(smask_h.data(), c->smask, smask_h.size() * 8, cudaMemcpyDeviceToHost,
+                                            c->stream));
             LBM_CREATE_CUDA(cudaMemcpyAsync(tiles_h.data(), c->non_empty, tiles_h.size() * 4, cudaMemcpyDeviceToHost,
                                             c->stream));
             LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
@@ -411,74 +415,80 @@ static lbm_status create_impl(const uint8_t* node_type, int on_device, int nx, i
             if (tz == ghost_lo) c->bnd_lo++;
             if (tz == c->Tz - 1 - ghost_hi) c->bnd_hi++;
         }
+        const int64_t n_own = c->own_k1 - c->own_k0;
         std::vector<int4> groups;
-        std::vector<uint32_t> fw, fi;
-        // fill lists: the solid and padding slots of every 32-byte sector that also holds a
-        // non-solid slot, per group (one list serves all 19 data blocks of a tile)
+        // fill lists (FP32): the solid and padding slots of every 32-byte sector that also
+        // holds a non-solid slot, per group (one list serves all 19 data blocks of a tile)
         std::vector<int2> fill_rng;
-        std::vector<uint32_t> fill;
+        std::vector<int64_t> lane0((size_t)n_own), fill0((size_t)n_own);
+        std::vector<uint8_t> lt((size_t)n_own);
         const int sector = lbm::fill_sector_slots(dtype);
         const int max_nodes = dtype == LBM_F64 ? lbm::GROUP_MAX_NODES_F64 : lbm::GROUP_MAX_NODES;
         const int max_tiles = dtype == LBM_F64 ? lbm::GROUP_MAX_TILES_F64 : lbm::GROUP_MAX_TILES_4B;
-        fw.reserve((size_t)nonsolid);
-        fi.reserve((size_t)nonsolid);
+        int64_t lanes = 0, fills = 0;
         int64_t k = c->own_k0;
         while (k < c->own_k1) {
             int4 g;
             g.x = (int)k;
             g.y = 0;
-            g.z = (int)fw.size();
+            g.z = (int)lanes;
             g.w = 0;
-            const size_t fill0 = fill.size();
+            const int64_t f_first = fills;
             while (k < c->own_k1 && g.y < max_tiles) {
-                int cnt = 0;
-                for (int sl = 0; sl < lbm::SLOTS; sl++) cnt += (words[k * lbm::SLOTS + sl] >> lbm::WORD_TYPE_SHIFT) != 0;
+                const int cnt = lbm::SLOTS - __builtin_popcountll(smask_h[k]);
                 if (g.w + cnt > max_nodes) break;
-                for (int sl = 0; sl < lbm::SLOTS; sl++) {
-                    const uint32_t w = words[k * lbm::SLOTS + sl];
-                    if ((w >> lbm::WORD_TYPE_SHIFT) == 0) continue;
-                    fw.push_back(w | ((uint32_t)g.y << lbm::WORD_LT_SHIFT) | ((uint32_t)sl << lbm::WORD_SLOT_SHIFT));
-                    fi.push_back((uint32_t)(k * lbm::SLOTS + sl));
-                }
-                const uint32_t* tw = &words[k * lbm::SLOTS];   // type 0: solid or padding
-                for (int sb = 0; sector > 0 && sb < lbm::SLOTS; sb += sector) {
-                    bool any = false;
-                    for (int sl = sb; sl < sb + sector; sl++) any |= (tw[sl] >> lbm::WORD_TYPE_SHIFT) != 0;
-                    if (!any) continue;
-                    for (int sl = sb; sl < sb + sector; sl++)
-                        if ((tw[sl] >> lbm::WORD_TYPE_SHIFT) == 0) fill.push_back((uint32_t)(g.y * lbm::SLOTS + sl));
-                }
+                lane0[k - c->own_k0] = lanes;
+                lt[k - c->own_k0] = (uint8_t)g.y;
+                fill0[k - c->own_k0] = fills;
+                lanes += cnt;
+                fills += __builtin_popcountll(lbm::fill_mask(smask_h[k], sector));
                 g.w += cnt;
                 g.y++;
                 k++;
             }
             groups.push_back(g);
-            fill_rng.push_back(make_int2((int)fill0, (int)(fill.size() - fill0)));
+            fill_rng.push_back(make_int2((int)f_first, (int)(fills - f_first)));
         }
         // the step updates the own tiles' nodes: in a slab context fewer than the box holds
-        if (ghost_lo == 0 && ghost_hi == 0 && (int64_t)fw.size() != c->n_nonsolid) {
+        if ((ghost_lo == 0 && ghost_hi == 0 && lanes != c->n_nonsolid) || lanes > 0x7fffffffll ||
+            fills > 0x7fffffffll) {
             fail(c, LBM_EINTERNAL, "non-solid node count mismatch while building work groups");
             return bail(LBM_EINTERNAL);
         }
-        c->n_own_nonsolid = (int64_t)fw.size();
+        c->n_own_nonsolid = lanes;
         c->n_groups = (int64_t)groups.size();
-        c->n_fill = (int64_t)fill.size();
+        c->n_fill = fills;
         LBM_CREATE_CUDA(dev_alloc(&c->gfill_rng, fill_rng.size()));
-        LBM_CREATE_CUDA(dev_alloc(&c->gfill, fill.size()));
-        if (!fill_rng.empty())
-            LBM_CREATE_CUDA(cudaMemcpyAsync(c->gfill_rng, fill_rng.data(), fill_rng.size() * sizeof(int2),
-                                            cudaMemcpyHostToDevice, c->stream));
-        if (!fill.empty())
-            LBM_CREATE_CUDA(cudaMemcpyAsync(c->gfill, fill.data(), fill.size() * sizeof(uint32_t),
-                                            cudaMemcpyHostToDevice, c->stream));
+        LBM_CREATE_CUDA(dev_alloc(&c->gfill, (size_t)fills));
         LBM_CREATE_CUDA(dev_alloc(&c->groups, groups.size()));
-        LBM_CREATE_CUDA(dev_alloc(&c->fword, fw.size()));
-        LBM_CREATE_CUDA(dev_alloc(&c->fidx, fi.size()));
+        LBM_CREATE_CUDA(dev_alloc(&c->fword, (size_t)lanes));
+        LBM_CREATE_CUDA(dev_alloc(&c->fidx, (size_t)lanes));
         if (!groups.empty()) {
-            LBM_CREATE_CUDA(cudaMemcpyAsync(c->groups, groups.data(), groups.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
-            LBM_CREATE_CUDA(cudaMemcpyAsync(c->fword, fw.data(), fw.size() * 4, cudaMemcpyHostToDevice, c->stream));
-            LBM_CREATE_CUDA(cudaMemcpyAsync(c->fidx, fi.data(), fi.size() * 4, cudaMemcpyHostToDevice, c->stream));
-            LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
+            int64_t* d_lane0 = nullptr;
+            int64_t* d_fill0 = nullptr;
+            uint8_t* d_lt = nullptr;
+            cudaError_t e = dev_alloc(&d_lane0, lane0.size());
+            if (e == cudaSuccess) e = dev_alloc(&d_fill0, fill0.size());
+            if (e == cudaSuccess) e = dev_alloc(&d_lt, lt.size());
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->groups, groups.data(), groups.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                                    c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(c->gfill_rng, fill_rng.data(), fill_rng.size() * sizeof(int2),
+                                    cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_lane0, lane0.data(), lane0.size() * 8, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_fill0, fill0.data(), fill0.size() * 8, cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_lt, lt.data(), lt.size(), cudaMemcpyHostToDevice, c->stream);
+            if (e == cudaSuccess) e = lbm::launch_lane_lists(c, d_lane0, d_lt, d_fill0, sector);
+            const cudaError_t e2 = cudaStreamSynchronize(c->stream);
+            lbm::dfree(d_lane0);
+            lbm::dfree(d_fill0);
+            lbm::dfree(d_lt);
+            LBM_CREATE_CUDA(e);
+            LBM_CREATE_CUDA(e2);
         }
     }
     c->p.omega = 1.0;

@@ -164,6 +164,20 @@ template <typename R> __host__ __device__ inline R par(double d, float f);
 template <> __host__ __device__ inline double par<double>(double d, float) { return d; }
 template <> __host__ __device__ inline float par<float>(double, float f) { return f; }
 
+// Solid slots (bits of smask) that share a sector of `sector` slots with a non-solid slot:
+// the fill slots of the FP32 step's full-sector writes. 0 for sector = 0.
+__host__ __device__ inline uint64_t fill_mask(uint64_t smask, int sector) {
+    uint64_t fm = 0;
+    if (sector <= 0) return 0;
+    const uint64_t sec = sector >= 64 ? ~0ull : (1ull << sector) - 1ull;
+    for (int b = 0; b < SLOTS; b += sector) {
+        const uint64_t m = (smask >> b) & sec;
+        if (m != sec) fm |= m << b;
+    }
+    return fm;
+}
+
+
 }  // namespace lbm
 
 struct lbm_ctx {
@@ -239,6 +253,7 @@ cudaError_t launch_scan_flags(const uint8_t* flag, int64_t n, int32_t* tile_map,
 int64_t scan_block_count(int64_t n);
 cudaError_t launch_tile_meta(lbm_ctx* c, const uint8_t* nt);
 cudaError_t launch_node_words(lbm_ctx* c);
+cudaError_t launch_lane_lists(lbm_ctx* c, const int64_t* lane0, const uint8_t* lt, const int64_t* fill0, int sector);
 cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]);
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B);
 cudaError_t launch_step_kind(lbm_ctx* c, int kind, const void* A, void* B);

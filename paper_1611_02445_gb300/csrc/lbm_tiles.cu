@@ -261,6 +261,39 @@ __global__ void k_init(typename Store<DT>::T* __restrict__ f0, typename Store<DT
     }
 }
 
+// The per-lane lists of the step's work groups (fword, fidx and, with fill lists, gfill),
+// from what the host decided per tile while forming the groups: the non-solid nodes of
+// tile k take lanes lane0[k], lane0[k] + 1, ... in slot order, lt[k] is the tile's index
+// within its group, and its fill entries start at fill0[k]. One CTA of 64 threads per tile,
+// one thread per slot; a slot's rank is the popcount of the tile's masks below it.
+__global__ void k_lane_lists(const uint32_t* __restrict__ nword, const uint64_t* __restrict__ smask,
+                             const int64_t* __restrict__ lane0, const uint8_t* __restrict__ lt,
+                             const int64_t* __restrict__ fill0, int sector, int64_t k0, int64_t k1,
+                             uint32_t* __restrict__ fword, uint32_t* __restrict__ fidx, uint32_t* __restrict__ gfill) {
+    const int s = threadIdx.x;
+    const uint64_t below = (1ull << s) - 1ull;   // s < 64
+    for (int64_t k = k0 + blockIdx.x; k < k1; k += gridDim.x) {
+        const uint64_t sm = smask[k];
+        const uint32_t l = lt[k - k0];
+        if (!((sm >> s) & 1ull)) {
+            const int64_t idx = lane0[k - k0] + __popcll(~sm & below);
+            fword[idx] = nword[k * SLOTS + s] | (l << WORD_LT_SHIFT) | ((uint32_t)s << WORD_SLOT_SHIFT);
+            fidx[idx] = (uint32_t)(k * SLOTS + s);
+        } else if (sector > 0) {
+            const uint64_t fm = fill_mask(sm, sector);
+            if ((fm >> s) & 1ull) gfill[fill0[k - k0] + __popcll(fm & below)] = l * SLOTS + (uint32_t)s;
+        }
+    }
+}
+
+cudaError_t launch_lane_lists(lbm_ctx* c, const int64_t* lane0, const uint8_t* lt, const int64_t* fill0, int sector) {
+    const int64_t n = c->own_k1 - c->own_k0;
+    if (n <= 0) return cudaSuccess;
+    k_lane_lists<<<(unsigned)std::min<int64_t>(n, 1 << 20), SLOTS, 0, c->stream>>>(
+        c->nword, c->smask, lane0, lt, fill0, sector, c->own_k0, c->own_k1, c->fword, c->fidx, c->gfill);
+    return cudaGetLastError();
+}
+
 static unsigned grid_for(int64_t n, int threads) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 32));
 }

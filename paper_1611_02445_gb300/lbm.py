@@ -376,11 +376,27 @@ def lbm_halo_bytes(ctx, side: int, pack: bool) -> int:
     return n.value
 
 
+def _halo_buffer(ctx, side: int, pack: bool, buf):
+    """A halo buffer is device memory of at least lbm_halo_bytes bytes: the library copies
+    into or out of it with device-to-device copies and cannot check it, so the binding
+    refuses anything else before the call."""
+    import torch
+    need = lbm_halo_bytes(ctx, side, pack)
+    if not isinstance(buf, torch.Tensor) or not buf.is_cuda or not buf.is_contiguous():
+        raise ValueError("halo buffers must be contiguous CUDA tensors")
+    if buf.numel() * buf.element_size() < need:
+        raise ValueError(f"halo buffer of {buf.numel() * buf.element_size()} bytes, needs {need}")
+
+
 def lbm_halo_pack(ctx, side: int, buf):
+    if lbm_halo_bytes(ctx, side, True):
+        _halo_buffer(ctx, side, True, buf)
     _check(load().lbm_halo_pack(ctx, int(side), _ptr(buf)), ctx)
 
 
 def lbm_halo_unpack(ctx, side: int, buf):
+    if lbm_halo_bytes(ctx, side, False):
+        _halo_buffer(ctx, side, False, buf)
     _check(load().lbm_halo_unpack(ctx, int(side), _ptr(buf)), ctx)
 
 

@@ -141,6 +141,15 @@ def test_halo_calls_need_a_ghost_plane():
         assert e.value.status == 5                                # LBM_ESTATE
     ctx = lbm.lbm_create_slab(nt, lbm.DTYPES["f64"], 0b011, 0, 2)  # bottom slab, z not periodic
     try:
+        import torch
+        lbm.lbm_set_params(ctx, 0.8)
+        lbm.lbm_init_equilibrium(ctx)
+        n = lbm.lbm_halo_bytes(ctx, 1, True)
+        assert n > 0
+        for bad in (np.zeros(n, np.uint8), torch.zeros(n, dtype=torch.uint8),
+                    torch.zeros(n - 1, dtype=torch.uint8, device="cuda")):
+            with pytest.raises(ValueError):                       # refused before the call
+                lbm.lbm_halo_pack(ctx, 1, bad)
         lbm.lbm_set_params(ctx, 0.8)
         lbm.lbm_init_equilibrium(ctx)
         with pytest.raises(lbm.LBMError) as e:
