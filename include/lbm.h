@@ -83,10 +83,11 @@ enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
 /* Build a context for one geometry: validate the node types, build the tile map on
  * the GPU (Algorithm 1 of Sec. 3.1: tile_flag -> exclusive scan in z-y-x tile order ->
  * scatter of tileMap and nonEmptyTiles), build per-tile neighbour tables and node
- * masks, the work groups of the step kernel (for FP32 storage with the lists of solid
- * slots that share a 32-byte sector with a non-solid slot: the step stores their NaN
- * again, so that it writes whole sectors), and allocate the two population copies A
- * and B (Sec. 3.1, "two copies").
+ * masks, the work groups of the step kernel, and allocate the two population copies A
+ * and B (Sec. 3.1, "two copies"). A copy stores the non-solid nodes only: the kept tiles
+ * are cut into groups of consecutive tiles with at most 256 non-solid nodes, and each
+ * group holds one 256-value block per direction (the nodes of a tile on consecutive
+ * positions in slot order, the unused positions zero).
  *   node_type   nx*ny*nz bytes, dense; host memory if on_device == 0, else a device
  *               pointer. Values other than 0..3 give LBM_EINVAL.
  *   tile        must be 4 (the paper's a = 4), else LBM_EUNSUPPORTED.
@@ -95,8 +96,9 @@ enum { LBM_PERIODIC_X = 1, LBM_PERIODIC_Y = 2, LBM_PERIODIC_Z = 4 };
  *               padded with solid nodes (Sec. 3.1).
  *   stream      cudaStream_t to queue work on (NULL = legacy default stream).
  *   out         receives the new context, or NULL on failure.
- * Limits: at most 2^31 / 64 kept tiles (2^31 node slots; per-node indices are 32-bit),
- * else LBM_EUNSUPPORTED; device memory for two population copies (LBM_ENOMEM).
+ * Limits: at most 2^31 / 64 kept tiles (2^31 node slots; per-node indices are 32-bit)
+ * and at most 2^31 / 256 groups, else LBM_EUNSUPPORTED; device memory for two population
+ * copies (LBM_ENOMEM).
  * The populations are not initialised: call lbm_init_equilibrium or lbm_set_f. */
 lbm_status lbm_create(const uint8_t* node_type, int on_device, int nx, int ny, int nz, int tile,
                       lbm_dtype dtype, unsigned periodic, void* stream, lbm_ctx** out);
@@ -231,7 +233,8 @@ lbm_status lbm_adjoint(lbm_ctx* ctx, int T, int ckpt_every, int plane_x, double*
  * indices t = tx + Tx (ty + Ty tz) in discovery order. Either array may be NULL. Host. */
 lbm_status lbm_get_tiles(lbm_ctx* ctx, int32_t* tile_map, uint32_t* non_empty, int64_t* n_tiles);
 
-/* Sizes: n_tiles kept, n_nonsolid nodes, bytes of one population copy. Any may be NULL. */
+/* Sizes: n_tiles kept, n_nonsolid nodes, bytes of one population copy (19 * 256 values per
+ * group, unused positions included). Any may be NULL. */
 lbm_status lbm_get_info(lbm_ctx* ctx, int64_t* n_tiles, int64_t* n_nonsolid, int64_t* copy_bytes);
 
 /* Copy the current state (the populations and, for LBM_F16S_SR, the step counter of the
@@ -290,13 +293,14 @@ lbm_status lbm_create_slab(const uint8_t* node_type, int nx, int ny, int nz, int
  *   side  0: the bottom of the box, 1: the top.
  *   lbm_halo_pack copies the populations the neighbouring slab on that side reads from
  *   this slab's boundary plane (side 0: the lowest own plane, directions with c_z = -1;
- *   side 1: the highest, c_z = +1) into buf, [direction][tile][64] in the stored format;
+ *   side 1: the highest, c_z = +1) into buf, [direction][tile][64] in the stored format
+ *   (NaN in the solid and padding slots);
  *   lbm_halo_unpack copies such a buffer, packed by that neighbour on the opposite side,
  *   into the ghost plane on this side. The two planes hold the same kept tiles in the
  *   same order, since both slabs were cut from the same geometry.
  *   lbm_halo_bytes gives the size of the buffer pack (pack = 1) or unpack (pack = 0)
  *   uses on that side: 5 * 64 * (bytes per value) per tile of the plane.
- *   buf   device pointer, on the context's stream; the copies are queued, not awaited.
+ *   buf   device pointer, on the context's stream; the copy kernel is queued, not awaited.
  * LBM_ESTATE if the box has no ghost plane on that side or no state is set. */
 lbm_status lbm_halo_bytes(lbm_ctx* ctx, int side, int pack, size_t* bytes);
 lbm_status lbm_halo_pack(lbm_ctx* ctx, int side, void* buf);

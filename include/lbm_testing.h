@@ -30,10 +30,10 @@ int64_t lbm_testing_live_allocations(void);
 void lbm_testing_fail_allocation(int64_t k);
 
 /* 1 if this library was built with LBM_CHECKED: the step kernel then tests every work-
- * group header, node tile, neighbour rank and fill entry against the context's arrays
- * before it uses them; a failed test skips the access and records (code << 56) | value
- * in the context's error word, and lbm_step / lbm_step_kernel return LBM_EINTERNAL
- * (sticky). Codes: 1 header or fill range, 2 node tile, 3 neighbour rank, 4 fill entry. */
+ * group header, node tile and gather source against the context's arrays before it uses
+ * them; a failed test skips the access and records (code << 56) | value in the context's
+ * error word, and lbm_step / lbm_step_kernel return LBM_EINTERNAL (sticky). Codes:
+ * 1 header, 2 node tile, 3 gather source outside the population copy. */
 int lbm_testing_checked_build(void);
 
 /* Checked build only: store `word` in the context's error word, as a failed check would,

@@ -32,6 +32,8 @@ template <int DT>
 __global__ void __launch_bounds__(LOSS_THREADS) k_loss_partials(const typename Store<DT>::T* __restrict__ f,
                                                                 const uint32_t* __restrict__ nword,
                                                                 const uint32_t* __restrict__ non_empty,
+                                                                const uint64_t* __restrict__ smask,
+                                                                const int32_t* __restrict__ tlane,
                                                                 const void* __restrict__ gfield, int64_t n_tiles,
                                                                 int Tx, int plane_x, StepParams p,
                                                                 double* __restrict__ partials) {
@@ -43,10 +45,11 @@ __global__ void __launch_bounds__(LOSS_THREADS) k_loss_partials(const typename S
         if ((nword[idx] >> WORD_TYPE_SHIFT) == LBM_SOLID) continue;
         const int x = TILE * (int)(non_empty[k] % (uint32_t)Tx) + (s & 3);
         if (x != plane_x) continue;
+        const uint32_t P = node_lane((uint32_t)tlane[k], smask[k], s);
         double r = 0.0, jx = 0.0;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const double v = to_f64<DT>(f[(k * Q + i) * SLOTS + s], i);
+            const double v = to_f64<DT>(f[data_index(P, i)], i);
             r += v;
             jx += cx(i) * v;
         }
@@ -85,7 +88,8 @@ __global__ void k_sum_partials(const double* __restrict__ partials, int nb, int 
 // elsewhere; the direct term dL/dF_x = -1/(2 rho |P|) starts the per-node gradient.
 template <int DT>
 __global__ void k_loss_seed(const typename Store<DT>::T* __restrict__ f, const uint32_t* __restrict__ nword,
-                            const uint32_t* __restrict__ non_empty, const void* __restrict__ gfield,
+                            const uint32_t* __restrict__ non_empty, const uint64_t* __restrict__ smask,
+                            const int32_t* __restrict__ tlane, const void* __restrict__ gfield,
                             int64_t n_tiles, int Tx, int plane_x, StepParams p, const double* __restrict__ sums,
                             Arith<DT>* __restrict__ lam, double* __restrict__ gbar) {
     using R = Arith<DT>;
@@ -94,15 +98,17 @@ __global__ void k_loss_seed(const typename Store<DT>::T* __restrict__ f, const u
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = idx >> 6;
         const int s = (int)(idx & 63);
-        bool on = (nword[idx] >> WORD_TYPE_SHIFT) != LBM_SOLID;
-        if (on) on = TILE * (int)(non_empty[k] % (uint32_t)Tx) + (s & 3) == plane_x;
+        const bool nonsolid = (nword[idx] >> WORD_TYPE_SHIFT) != LBM_SOLID;
+        if (!nonsolid) continue;   // solid slots have no storage
+        const uint32_t P = node_lane((uint32_t)tlane[k], smask[k], s);
+        const bool on = TILE * (int)(non_empty[k] % (uint32_t)Tx) + (s & 3) == plane_x;
         double r = 1.0, ux = 0.0;
         if (on) {
             double jx = 0.0;
             r = 0.0;
 #pragma unroll
             for (int i = 0; i < Q; i++) {
-                const double v = to_f64<DT>(f[(k * Q + i) * SLOTS + s], i);
+                const double v = to_f64<DT>(f[data_index(P, i)], i);
                 r += v;
                 jx += cx(i) * v;
             }
@@ -110,7 +116,7 @@ __global__ void k_loss_seed(const typename Store<DT>::T* __restrict__ f, const u
             ux = (jx - 0.5 * Fx) / r;
         }
 #pragma unroll
-        for (int i = 0; i < Q; i++) lam[(k * Q + i) * SLOTS + s] = on ? (R)((cx(i) - ux) / (r * count)) : R(0);
+        for (int i = 0; i < Q; i++) lam[data_index(P, i)] = on ? (R)((cx(i) - ux) / (r * count)) : R(0);
         gbar[idx] = on ? -0.5 / (r * count) : 0.0;
     }
 }
@@ -212,6 +218,8 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const typename Store<DT
                                                          const Arith<DT>* __restrict__ mu_in, int direct,
                                                          Arith<DT>* __restrict__ mu_out,
                                                          const int32_t* __restrict__ nbr,
+                                                         const uint64_t* __restrict__ smask,
+                                                         const int32_t* __restrict__ tlane,
                                                          const uint32_t* __restrict__ fword,
                                                          const uint32_t* __restrict__ fidx,
                                                          const void* __restrict__ gfield, int64_t n_nodes,
@@ -228,7 +236,7 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const typename Store<DT
         const int64_t k = gi >> 6;
         const int s = (int)(gi & 63u);
         const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
-        const int64_t own = k * (Q * SLOTS);
+        const uint32_t own = node_lane((uint32_t)__ldg(tlane + k), __ldg(smask + k), s);
         R v[Q], lam[Q], mu[Q];
 #pragma unroll
         for (int i = 0; i < Q; i++) {
@@ -238,20 +246,23 @@ __global__ void __launch_bounds__(ADJ_THREADS) k_adjoint(const typename Store<DT
             const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
             const int ss = (sx & 3) | ((sy & 3) << 2) | ((sz & 3) << 4);
             const bool bounce = (w >> i) & 1;
-            const int64_t base = bounce ? 0 : (nb == 13 ? own : (int64_t)__ldg(nbr + k * NBR_STRIDE + nb) * (Q * SLOTS));
-            const int64_t src = bounce ? own + inv(i) * SLOTS + s : base + i * SLOTS + ss;
-            v[i] = to_arith<DT>(st[src], i);
+            uint32_t src = own;
+            if (!bounce) {
+                const int64_t r = nb == 13 ? k : (int64_t)__ldg(nbr + k * NBR_STRIDE + nb);
+                src = node_lane((uint32_t)__ldg(tlane + r), __ldg(smask + r), ss);
+            }
+            v[i] = to_arith<DT>(st[data_index(src, bounce ? inv(i) : i)], i);
             if (direct) {
-                lam[inv(i)] = mu_in[own + inv(i) * SLOTS + s];
+                lam[inv(i)] = mu_in[data_index(own, inv(i))];
             } else {
-                lam[inv(i)] = bounce ? mu_in[own + i * SLOTS + s] : mu_in[base + inv(i) * SLOTS + ss];
+                lam[inv(i)] = mu_in[data_index(src, bounce ? i : inv(i))];
             }
         }
         const R Fx = gfield ? (R)gfield_at<DT>(gfield, (int64_t)gi) : par<R>(p.g[0], p.g_f[0]);
         const R Fb = collide_adjoint<R, Store<DT>::SHIFT>(v, lam, type, p, Fx, par<R>(p.g[1], p.g_f[1]),
                                                           par<R>(p.g[2], p.g_f[2]), mu, taubar);
 #pragma unroll
-        for (int i = 0; i < Q; i++) mu_out[own + i * SLOTS + s] = mu[i];
+        for (int i = 0; i < Q; i++) mu_out[data_index(own, i)] = mu[i];
         gbar[gi] += (double)Fb;
     }
     for (int o = 16; o > 0; o >>= 1) taubar += __shfl_down_sync(0xffffffffu, taubar, o);
@@ -297,12 +308,12 @@ cudaError_t run_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, dou
     using TT = typename Store<DT>::T;
     using R = Arith<DT>;
     cudaError_t e;
-    const size_t copy = (size_t)c->n_tiles * Q * SLOTS * sizeof(TT);
+    const size_t copy = (size_t)c->n_sgroups * Q * GROUP_LANES * sizeof(TT);
     const int64_t n_slots = c->n_tiles * SLOTS;
     const bool grads = dL_dg || dL_dtau;
     const int n_ck = (T + K - 1) / K;
     const int seg_len = std::min(K, T);
-    const size_t mu_bytes = (size_t)c->n_tiles * Q * SLOTS * sizeof(R);
+    const size_t mu_bytes = (size_t)c->n_sgroups * Q * GROUP_LANES * sizeof(R);
     const int adj_blocks = (int)std::max<int64_t>(1, (c->n_own_nonsolid + ADJ_THREADS - 1) / ADJ_THREADS);
     const int nbl = (int)std::max<int64_t>(1, std::min<int64_t>((n_slots + LOSS_THREADS - 1) / LOSS_THREADS, 152 * 4));
     const size_t N = (size_t)c->nx * c->ny * c->nz;
@@ -334,7 +345,8 @@ cudaError_t run_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, dou
     }
     // loss on s_T
     const TT* sT = static_cast<const TT*>(c->f[c->cur]);
-    k_loss_partials<DT><<<nbl, LOSS_THREADS, 0, c->stream>>>(sT, c->nword, c->non_empty, c->gfield, c->n_tiles, c->Tx,
+    k_loss_partials<DT><<<nbl, LOSS_THREADS, 0, c->stream>>>(sT, c->nword, c->non_empty, c->smask, c->tlane, c->gfield,
+                                                             c->n_tiles, c->Tx,
                                                              plane_x, c->p, static_cast<double*>(lossp.p));
     k_sum_partials<<<1, 32, 0, c->stream>>>(static_cast<const double*>(lossp.p), nbl, 2, static_cast<double*>(sums.p));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -355,7 +367,8 @@ cudaError_t run_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, dou
     R* mu[2] = {static_cast<R*>(mu0.p), static_cast<R*>(mu1.p)};
     int mcur = 0;
     const unsigned gs = (unsigned)std::max<int64_t>(1, std::min<int64_t>((n_slots + 255) / 256, 152 * 32));
-    k_loss_seed<DT><<<gs, 256, 0, c->stream>>>(sT, c->nword, c->non_empty, c->gfield, c->n_tiles, c->Tx, plane_x, c->p,
+    k_loss_seed<DT><<<gs, 256, 0, c->stream>>>(sT, c->nword, c->non_empty, c->smask, c->tlane, c->gfield, c->n_tiles,
+                                               c->Tx, plane_x, c->p,
                                                static_cast<const double*>(sums.p), mu[mcur],
                                                static_cast<double*>(gbar.p));
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -371,7 +384,7 @@ cudaError_t run_adjoint(lbm_ctx* c, int T, int K, int plane_x, double* loss, dou
         for (int t = t1 - 1; t >= t0; t--) {
             k_adjoint<DT><<<adj_blocks, ADJ_THREADS, 0, c->stream>>>(
                 reinterpret_cast<const TT*>(sb + copy * (t - t0)), mu[mcur], direct ? 1 : 0, mu[1 - mcur], c->nbr,
-                c->fword, c->fidx, c->gfield, c->n_own_nonsolid, c->p, static_cast<double*>(gbar.p),
+                c->smask, c->tlane, c->fword, c->fidx, c->gfield, c->n_own_nonsolid, c->p, static_cast<double*>(gbar.p),
                 static_cast<double*>(taup.p));
             if ((e = cudaGetLastError()) != cudaSuccess) return e;
             mcur ^= 1;

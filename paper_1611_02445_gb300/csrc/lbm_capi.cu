@@ -128,7 +128,7 @@ void free_all(lbm_ctx* c) {
     drop_graphs(c);
     void* bufs[] = {c->tile_map, c->non_empty, c->nbr,    c->smask,  c->tflags, c->ntype,    c->nword,
                     c->groups,   c->fword,     c->fidx,   c->gfield, c->gfield_c, c->f[0], c->f[1],
-                    c->partials, c->d_out, c->seed, c->gfill_rng, c->gfill, c->check};
+                    c->partials, c->d_out, c->seed, c->tlane, c->nrec, c->frank, c->check};
     for (void* b : bufs)
         if (b) lbm::dfree(b);
     c->tile_map = nullptr;
@@ -141,8 +141,9 @@ void free_all(lbm_ctx* c) {
     c->groups = nullptr;
     c->fword = nullptr;
     c->fidx = nullptr;
-    c->gfill_rng = nullptr;
-    c->gfill = nullptr;
+    c->tlane = nullptr;
+    c->nrec = nullptr;
+    c->frank = nullptr;
     c->gfield_c = nullptr;
     c->f[0] = c->f[1] = nullptr;
     c->gfield = nullptr;
@@ -219,12 +220,11 @@ lbm_status read_check(lbm_ctx* c) {
     LBM_CUDA(c, cudaMemcpyAsync(&word, c->check, sizeof(word), cudaMemcpyDeviceToHost, c->stream));
     LBM_CUDA(c, cudaStreamSynchronize(c->stream));
     if (word == 0) return LBM_OK;
-    static const char* what[] = {"?", "work-group header or fill range out of range", "node tile not in its group",
-                                 "neighbour rank of a pulled direction not a kept tile",
-                                 "fill entry tile not in its group"};
+    static const char* what[] = {"?", "work-group header out of range", "node tile not in its group",
+                                 "gather source of a pulled direction outside the population copy"};
     const unsigned code = (unsigned)(word >> 56);
     return fail(c, LBM_EINTERNAL,
-                std::string("checked build: step kernel index check failed (") + what[code < 5 ? code : 0] +
+                std::string("checked build: step kernel index check failed (") + what[code < 4 ? code : 0] +
                     ", code " + std::to_string(code) + ", value " + std::to_string(word & 0x00ffffffffffffffull) +
                     "); the access was skipped");
 }
@@ -347,7 +347,6 @@ static lbm_status create_impl(const uint8_t* node_type, int on_device, int nx, i
         return bail(LBM_EUNSUPPORTED);
     }
     c->n_tiles = count;
-    const size_t copy_bytes = (size_t)count * lbm::Q * lbm::SLOTS * lbm::dtype_size(dtype);
     c->n_partials = lbm::reduce_blocks(count);
     LBM_CREATE_CUDA(dev_alloc(&c->nbr, (size_t)count * lbm::NBR_STRIDE));
     LBM_CREATE_CUDA(dev_alloc(&c->nword, (size_t)count * lbm::SLOTS));
@@ -356,8 +355,6 @@ static lbm_status create_impl(const uint8_t* node_type, int on_device, int nx, i
     LBM_CREATE_CUDA(dev_alloc(&c->ntype, (size_t)count * lbm::SLOTS));
     LBM_CREATE_CUDA(dev_alloc(&c->partials, (size_t)c->n_partials * 4));
     LBM_CREATE_CUDA(dev_alloc(&c->d_out, 8));
-    LBM_CREATE_CUDA(lbm::dmalloc(&c->f[0], std::max<size_t>(copy_bytes, 16)));
-    LBM_CREATE_CUDA(lbm::dmalloc(&c->f[1], std::max<size_t>(copy_bytes, 16)));
 #ifdef LBM_CHECKED
     LBM_CREATE_CUDA(dev_alloc(&c->check, 1));
     LBM_CREATE_CUDA(cudaMemsetAsync(c->check, 0, sizeof(unsigned long long), c->stream));
@@ -416,87 +413,104 @@ static lbm_status create_impl(const uint8_t* node_type, int on_device, int nx, i
             if (tz == c->Tz - 1 - ghost_hi) c->bnd_hi++;
         }
         const int64_t n_own = c->own_k1 - c->own_k0;
+        // Storage groups, formed greedily over the lower ghost plane, the own tiles and the
+        // upper ghost plane separately (the step updates whole groups of own tiles): each
+        // tile gets its padded lane tlane, and the own groups become the step's work groups.
         std::vector<int4> groups;
-        // fill lists (FP32): the solid and padding slots of every 32-byte sector that also
-        // holds a non-solid slot, per group (one list serves all 19 data blocks of a tile)
-        std::vector<int2> fill_rng;
-        std::vector<int64_t> lane0((size_t)n_own), fill0((size_t)n_own);
+        std::vector<int32_t> tlane_h((size_t)count);
+        std::vector<int64_t> lane0((size_t)n_own);
         std::vector<uint8_t> lt((size_t)n_own);
-        const int sector = lbm::fill_sector_slots(dtype);
         const int max_nodes = dtype == LBM_F64 ? lbm::GROUP_MAX_NODES_F64 : lbm::GROUP_MAX_NODES;
         const int max_tiles = dtype == LBM_F64 ? lbm::GROUP_MAX_TILES_F64 : lbm::GROUP_MAX_TILES_4B;
-        int64_t lanes = 0, fills = 0;
-        int64_t k = c->own_k0;
-        while (k < c->own_k1) {
-            int4 g;
-            g.x = (int)k;
-            g.y = 0;
-            g.z = (int)lanes;
-            g.w = 0;
-            const int64_t f_first = fills;
-            while (k < c->own_k1 && g.y < max_tiles) {
-                const int cnt = lbm::SLOTS - __builtin_popcountll(smask_h[k]);
-                if (g.w + cnt > max_nodes) break;
-                lane0[k - c->own_k0] = lanes;
-                lt[k - c->own_k0] = (uint8_t)g.y;
-                fill0[k - c->own_k0] = fills;
-                lanes += cnt;
-                fills += __builtin_popcountll(lbm::fill_mask(smask_h[k], sector));
-                g.w += cnt;
-                g.y++;
-                k++;
+        int64_t sgroups = 0, lanes = 0;
+        auto form = [&](int64_t k0, int64_t k1, bool own) {
+            int64_t k = k0;
+            while (k < k1) {
+                int4 g;
+                g.x = (int)k;
+                g.y = 0;
+                g.z = (int)lanes;
+                g.w = 0;
+                while (k < k1 && g.y < max_tiles) {
+                    const int cnt = lbm::SLOTS - __builtin_popcountll(smask_h[k]);
+                    if (g.w + cnt > max_nodes) break;
+                    tlane_h[k] = (int32_t)(sgroups * lbm::GROUP_LANES + g.w);
+                    if (own) {
+                        lane0[k - c->own_k0] = lanes;
+                        lt[k - c->own_k0] = (uint8_t)g.y;
+                        lanes += cnt;
+                    }
+                    g.w += cnt;
+                    g.y++;
+                    k++;
+                }
+                if (own) groups.push_back(g);
+                sgroups++;
+                if (sgroups > 0x7fffffffll / lbm::GROUP_LANES) return false;
             }
-            groups.push_back(g);
-            fill_rng.push_back(make_int2((int)f_first, (int)(fills - f_first)));
+            return true;
+        };
+        bool fits = form(0, c->own_k0, false);
+        c->p.sg0 = sgroups;
+        fits = fits && form(c->own_k0, c->own_k1, true) && form(c->own_k1, count, false);
+        if (!fits) {
+            // padded lanes are 32-bit
+            fail(c, LBM_EUNSUPPORTED, "more than 2^31 padded node lanes are not supported");
+            return bail(LBM_EUNSUPPORTED);
         }
         // the step updates the own tiles' nodes: in a slab context fewer than the box holds
-        if ((ghost_lo == 0 && ghost_hi == 0 && lanes != c->n_nonsolid) || lanes > 0x7fffffffll ||
-            fills > 0x7fffffffll) {
+        if ((ghost_lo == 0 && ghost_hi == 0 && lanes != c->n_nonsolid) || lanes > 0x7fffffffll) {
             fail(c, LBM_EINTERNAL, "non-solid node count mismatch while building work groups");
             return bail(LBM_EINTERNAL);
         }
         c->n_own_nonsolid = lanes;
         c->n_groups = (int64_t)groups.size();
-        c->n_fill = fills;
-        LBM_CREATE_CUDA(dev_alloc(&c->gfill_rng, fill_rng.size()));
-        LBM_CREATE_CUDA(dev_alloc(&c->gfill, (size_t)fills));
+        c->n_sgroups = sgroups;
+        const size_t copy_bytes = (size_t)sgroups * lbm::Q * lbm::GROUP_LANES * lbm::dtype_size(dtype);
+        LBM_CREATE_CUDA(lbm::dmalloc(&c->f[0], std::max<size_t>(copy_bytes, 16)));
+        LBM_CREATE_CUDA(lbm::dmalloc(&c->f[1], std::max<size_t>(copy_bytes, 16)));
+        // the padding lanes of the groups are never read or written: zero, so that a saved
+        // state depends on the populations alone
+        LBM_CREATE_CUDA(cudaMemsetAsync(c->f[0], 0, copy_bytes, c->stream));
+        LBM_CREATE_CUDA(cudaMemsetAsync(c->f[1], 0, copy_bytes, c->stream));
+        LBM_CREATE_CUDA(dev_alloc(&c->tlane, (size_t)std::max<int64_t>(count, 1)));
+        LBM_CREATE_CUDA(dev_alloc(&c->nrec, (size_t)std::max<int64_t>(count, 1) * lbm::NBR_STRIDE));
         LBM_CREATE_CUDA(dev_alloc(&c->groups, groups.size()));
         LBM_CREATE_CUDA(dev_alloc(&c->fword, (size_t)lanes));
         LBM_CREATE_CUDA(dev_alloc(&c->fidx, (size_t)lanes));
+        LBM_CREATE_CUDA(dev_alloc(&c->frank, (size_t)lanes));
+        if (count > 0) {
+            LBM_CREATE_CUDA(cudaMemcpyAsync(c->tlane, tlane_h.data(), tlane_h.size() * sizeof(int32_t),
+                                            cudaMemcpyHostToDevice, c->stream));
+            LBM_CREATE_CUDA(lbm::launch_node_records(c));
+        }
         if (!groups.empty()) {
             int64_t* d_lane0 = nullptr;
-            int64_t* d_fill0 = nullptr;
             uint8_t* d_lt = nullptr;
             cudaError_t e = dev_alloc(&d_lane0, lane0.size());
-            if (e == cudaSuccess) e = dev_alloc(&d_fill0, fill0.size());
             if (e == cudaSuccess) e = dev_alloc(&d_lt, lt.size());
             if (e == cudaSuccess)
                 e = cudaMemcpyAsync(c->groups, groups.data(), groups.size() * sizeof(int4), cudaMemcpyHostToDevice,
                                     c->stream);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(c->gfill_rng, fill_rng.data(), fill_rng.size() * sizeof(int2),
-                                    cudaMemcpyHostToDevice, c->stream);
-            if (e == cudaSuccess)
                 e = cudaMemcpyAsync(d_lane0, lane0.data(), lane0.size() * 8, cudaMemcpyHostToDevice, c->stream);
             if (e == cudaSuccess)
-                e = cudaMemcpyAsync(d_fill0, fill0.data(), fill0.size() * 8, cudaMemcpyHostToDevice, c->stream);
-            if (e == cudaSuccess)
                 e = cudaMemcpyAsync(d_lt, lt.data(), lt.size(), cudaMemcpyHostToDevice, c->stream);
-            if (e == cudaSuccess) e = lbm::launch_lane_lists(c, d_lane0, d_lt, d_fill0, sector);
+            if (e == cudaSuccess) e = lbm::launch_lane_lists(c, d_lane0, d_lt);
             const cudaError_t e2 = cudaStreamSynchronize(c->stream);
             lbm::dfree(d_lane0);
-            lbm::dfree(d_fill0);
             lbm::dfree(d_lt);
             LBM_CREATE_CUDA(e);
             LBM_CREATE_CUDA(e2);
         }
+        LBM_CREATE_CUDA(cudaStreamSynchronize(c->stream));
     }
     c->p.omega = 1.0;
     c->p.beta = 0.5;
     c->p.rho_out = 1.0;
     c->p.n_tiles = c->n_tiles;
     c->p.n_lanes = c->n_own_nonsolid;
-    c->p.n_fill = c->n_fill;
+    c->p.n_padded = c->n_sgroups * lbm::GROUP_LANES;
     c->p.check = c->check;
     cleanup();
 #undef LBM_CREATE_CUDA
@@ -903,14 +917,14 @@ lbm_status lbm_get_info(lbm_ctx* c, int64_t* n_tiles, int64_t* n_nonsolid, int64
     LBM_CHECK_CTX(c);
     if (n_tiles) *n_tiles = c->n_tiles;
     if (n_nonsolid) *n_nonsolid = c->n_own_nonsolid;
-    if (copy_bytes) *copy_bytes = c->n_tiles * lbm::Q * lbm::SLOTS * (int64_t)lbm::dtype_size(c->dtype);
+    if (copy_bytes) *copy_bytes = c->n_sgroups * lbm::Q * lbm::GROUP_LANES * (int64_t)lbm::dtype_size(c->dtype);
     return LBM_OK;
 }
 
 lbm_status lbm_save_state(lbm_ctx* c, void* blob, size_t* nbytes) {
     LBM_CHECK_CTX(c);
     if (!nbytes) return fail(c, LBM_EINVAL, "nbytes is NULL");
-    const size_t payload = (size_t)c->n_tiles * lbm::Q * lbm::SLOTS * lbm::dtype_size(c->dtype);
+    const size_t payload = (size_t)c->n_sgroups * lbm::Q * lbm::GROUP_LANES * lbm::dtype_size(c->dtype);
     const size_t total = sizeof(StateHeader) + payload;
     if (!blob) {
         *nbytes = total;
@@ -920,7 +934,7 @@ lbm_status lbm_save_state(lbm_ctx* c, void* blob, size_t* nbytes) {
     if (!c->state_set) return fail(c, LBM_ESTATE, "no state");
     StateHeader h{};
     std::memcpy(h.magic, "LBMGB300", 8);
-    h.version = 2;
+    h.version = 3;
     h.dtype = c->dtype;
     h.nx = c->nx; h.ny = c->ny; h.nz = c->nz;
     h.periodic = c->periodic;
@@ -943,8 +957,8 @@ lbm_status lbm_load_state(lbm_ctx* c, const void* blob, size_t nbytes) {
     if (!blob || nbytes < sizeof(StateHeader)) return fail(c, LBM_ESTATE, "blob too small");
     StateHeader h;
     std::memcpy(&h, blob, sizeof(h));
-    const size_t payload = (size_t)c->n_tiles * lbm::Q * lbm::SLOTS * lbm::dtype_size(c->dtype);
-    if (std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2) return fail(c, LBM_ESTATE, "not a state blob");
+    const size_t payload = (size_t)c->n_sgroups * lbm::Q * lbm::GROUP_LANES * lbm::dtype_size(c->dtype);
+    if (std::memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 3) return fail(c, LBM_ESTATE, "not a state blob");
     if (h.dtype != c->dtype || h.nx != c->nx || h.ny != c->ny || h.nz != c->nz || h.periodic != c->periodic ||
         h.n_tiles != c->n_tiles || h.payload_bytes != payload || nbytes < sizeof(h) + payload)
         return fail(c, LBM_ESTATE, "state blob is for another geometry or dtype");

@@ -13,25 +13,37 @@
 //   smask    [n_tiles]   uint64  bit s set when node s of the tile is solid or padding
 //   tflags   [n_tiles]   uint32  bit 0: the tile holds inlet or outlet nodes
 //   ntype    [n_tiles][64] uint8 node types in slot order (the per-tile nodeType block)
-//   f[2]     [n_tiles][19][64]   populations, tile-major SoA: one 64-value data block
-//                               per direction per tile (Sec. 3.2, Fig. 3), slot
-//                               s = x + 4 y + 16 z inside the tile (Eq. 11 order)
+//   f[2]     [n_sgroups][19][256] populations of the non-solid nodes only, grouped: the
+//                               kept tiles are cut into storage groups of consecutive
+//                               tiles with at most 256 non-solid nodes (the step's work
+//                               groups, plus those of a slab's ghost planes), and a group
+//                               holds one 256-value data block per direction. A node's
+//                               padded lane is P = 256 * group + its lane in the group;
+//                               the lanes of a tile are consecutive in slot order, so the
+//                               node in slot s of tile k has P = tlane[k] + (non-solid
+//                               slots of the tile below s), and f_i lives at
+//                               (P / 256) * 19 * 256 + 256 i + P % 256 (data_index)
+//   tlane    [n_tiles]   int32   padded lane of each tile's first non-solid node
+//   nrec     [n_tiles][28] int64 the step's neighbour records: for the 3x3x3 tile
+//                               neighbourhood (index 13 + dx + 3 dy + 9 dz) the index in a
+//                               copy of the neighbour's first non-solid node in data block
+//                               0; zero for dropped or out-of-box tiles, which no gather
+//                               reads (their links bounce back); entry 27 is padding so
+//                               each record is 224 bytes, 16-byte aligned
 //   gfield   [n_tiles][64]       optional per-node x force (double for F64, else float)
 //   groups   [n_groups] int4     work units of the step kernel: {first tile, tiles (<= 16
 //                               for FP64 storage, <= 8 otherwise), first fluid node, fluid
-//                               nodes (<= 256)}, consecutive tiles
+//                               nodes (<= 256)}, consecutive tiles; work group g is
+//                               storage group sg0 + g
 //   fword    [n_fluid] uint32    the gather word of every non-solid node in group order,
 //                               plus bit 19 set when the node lies on the moving lid face
 //                               (lbm_set_lid), bits 22-25 its tile within the group and
 //                               bits 26-31 its slot
 //   fidx     [n_fluid] uint32    k * 64 + s of every non-solid node in the same order
-//   gfill_rng[n_groups]  int2    {first entry, entries} of each work group's fill list
-//   gfill    [n_fill]    uint32  (tile within the group) * 64 + slot of every solid or padding
-//                               slot that shares a 32-byte sector of a data block with a
-//                               non-solid slot: the step stores NaN there (the value the slot
-//                               already holds), so that every sector it writes is written
-//                               whole and DRAM never has to merge a partial sector (FP32
-//                               storage only; empty for the other formats)
+//   frank    [n_fluid] uint4     per node and pulled direction i (1..18) the rank of the
+//                               source slot among its tile's non-solid slots, 6 bits each,
+//                               five directions per word (rank_of); 0 for a bounced link.
+//                               f_i(x - c_i) then lives at nrec[tile][nb] + 256 i + rank
 //   gfield_c [n_fluid]           the per-node force in the same order
 #pragma once
 
@@ -59,18 +71,13 @@ constexpr int WORD_SLOT_SHIFT = 26;    // compact words: slot in the tile (6 bit
 constexpr int GROUP_MAX_TILES_F64 = 16;   // tiles per work group: FP64 storage
 constexpr int GROUP_MAX_TILES_4B = 8;     // and the 4-byte-or-smaller formats
 constexpr int GRAPH_STEPS = 16;
-// Slots per 32-byte sector that the step writes whole (the fill lists), per storage
-// format; 0 for none. Only FP32 storage uses them: there the step is bound by DRAM
-// traffic, and the merge reads of partly written sectors cost more than the extra stores.
-// The FP64 and FP16 steps are bound by instruction issue and the load/store queue, and the
-// scattered fill stores made them 5 % and 10 % slower although DRAM reads fell by a quarter.
-constexpr int fill_sector_slots(int dtype) { return dtype == LBM_F32 ? 8 : 0; }
 // kernel kinds: the fused step and the paper's two calibration kernels (Sec. 4.1)
 constexpr int STEP_FULL = 0;        // gather, collide, store
 constexpr int STEP_PROPAGATE = 1;   // gather with bounce-back and store ("propagation only")
 constexpr int STEP_RW = 2;          // read and write each node's own values ("read/write only")
 constexpr int GROUP_MAX_NODES = 256;       // work-group size of the 4-byte-or-smaller formats
 constexpr int GROUP_MAX_NODES_F64 = 256;   // and of FP64 storage (see the step kernel's CTA shape)
+constexpr int GROUP_LANES = 256;           // lanes of a storage group: the length of its data blocks
 constexpr int FLAG_HAS_BC = 1;
 // F16S storage scale: h is stored as half(h * 2^12), so |h| in [1.5e-8, 16] is normal.
 constexpr float F16_SCALE = 4096.0f;
@@ -99,6 +106,23 @@ __host__ __device__ constexpr int inv(int i) {
 }
 __host__ __device__ constexpr double wgt(int i) {
     return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0);
+}
+
+// Index of f_i of the node with padded lane P in a copy of the populations (the grouped
+// layout above): data block i of storage group P / 256, position P % 256.
+__host__ __device__ inline int64_t data_index(uint32_t P, int i) {
+    return (int64_t)(P / GROUP_LANES) * (Q * GROUP_LANES) + i * GROUP_LANES + (P % GROUP_LANES);
+}
+// Rank of direction i's source slot (i = 1..18) in a node's rank words (frank).
+__host__ __device__ inline uint32_t rank_of(const uint4& r, int i) {
+    const int w = (i - 1) / 5, b = 6 * ((i - 1) % 5);
+    const uint32_t v = w == 0 ? r.x : w == 1 ? r.y : w == 2 ? r.z : r.w;
+    return (v >> b) & 63u;
+}
+// Padded lane of the non-solid slot s of a tile whose first non-solid node has padded
+// lane tl and whose solid mask is sm: tl plus the non-solid slots below s.
+__device__ __forceinline__ uint32_t node_lane(uint32_t tl, uint64_t sm, int s) {
+    return tl + (uint32_t)__popcll(~sm & ((1ull << s) - 1ull));
 }
 
 // Storage traits: element type T in HBM and arithmetic type R.
@@ -145,38 +169,26 @@ struct StepParams {
     // LBM_BC_ZOU_HE with the box faces of the inlet and the outlet nodes
     int bc;
     int zh_face[2];
-    // extents the checked build (LBM_CHECKED) tests every index against, and its error
-    // word (NULL in the normal build): the first failed check stores (code << 56) | value
-    int64_t n_tiles, n_lanes, n_fill;
+    // storage group of work group 0 (a slab's lower ghost plane has groups before it)
+    int64_t sg0;
+    // extents the checked build (LBM_CHECKED) tests every index against (kept tiles,
+    // non-solid nodes of the work groups, padded lanes of a copy), and its error word
+    // (NULL in the normal build): the first failed check stores (code << 56) | value
+    int64_t n_tiles, n_lanes, n_padded;
     unsigned long long* check;
 };
 
 // Codes of the checked build's error word.
 enum : unsigned {
-    CHECK_HEADER = 1,      // a work-group header or fill range outside the context's arrays
+    CHECK_HEADER = 1,      // a work-group header outside the context's arrays
     CHECK_OWN_TILE = 2,    // a node word whose tile is not in its group
-    CHECK_NEIGHBOUR = 3,   // a pulled direction whose neighbour rank is not a kept tile
-    CHECK_FILL = 4         // a fill-list entry whose tile is not in its group
+    CHECK_NEIGHBOUR = 3    // a pulled direction whose source lane lies outside the copy
 };
 
 // A parameter in the arithmetic type R: the FP64 value or its FP32 copy.
 template <typename R> __host__ __device__ inline R par(double d, float f);
 template <> __host__ __device__ inline double par<double>(double d, float) { return d; }
 template <> __host__ __device__ inline float par<float>(double, float f) { return f; }
-
-// Solid slots (bits of smask) that share a sector of `sector` slots with a non-solid slot:
-// the fill slots of the FP32 step's full-sector writes. 0 for sector = 0.
-__host__ __device__ inline uint64_t fill_mask(uint64_t smask, int sector) {
-    uint64_t fm = 0;
-    if (sector <= 0) return 0;
-    const uint64_t sec = sector >= 64 ? ~0ull : (1ull << sector) - 1ull;
-    for (int b = 0; b < SLOTS; b += sector) {
-        const uint64_t m = (smask >> b) & sec;
-        if (m != sec) fm |= m << b;
-    }
-    return fm;
-}
-
 
 }  // namespace lbm
 
@@ -213,9 +225,10 @@ struct lbm_ctx {
     int4* groups = nullptr;
     uint32_t* fword = nullptr;
     uint32_t* fidx = nullptr;
-    int2* gfill_rng = nullptr;
-    uint32_t* gfill = nullptr;
-    int64_t n_fill = 0;
+    int32_t* tlane = nullptr;
+    int64_t* nrec = nullptr;
+    uint4* frank = nullptr;
+    int64_t n_sgroups = 0;      // storage groups of a copy (work groups and ghost-plane groups)
     void* gfield_c = nullptr;
     int64_t n_groups = 0;
     void* f[2] = {nullptr, nullptr};
@@ -253,7 +266,8 @@ cudaError_t launch_scan_flags(const uint8_t* flag, int64_t n, int32_t* tile_map,
 int64_t scan_block_count(int64_t n);
 cudaError_t launch_tile_meta(lbm_ctx* c, const uint8_t* nt);
 cudaError_t launch_node_words(lbm_ctx* c);
-cudaError_t launch_lane_lists(lbm_ctx* c, const int64_t* lane0, const uint8_t* lt, const int64_t* fill0, int sector);
+cudaError_t launch_lane_lists(lbm_ctx* c, const int64_t* lane0, const uint8_t* lt);
+cudaError_t launch_node_records(lbm_ctx* c);
 cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]);
 cudaError_t launch_step(lbm_ctx* c, const void* A, void* B);
 cudaError_t launch_step_kind(lbm_ctx* c, int kind, const void* A, void* B);

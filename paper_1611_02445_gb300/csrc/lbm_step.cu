@@ -20,9 +20,12 @@
 //             or Zou-He completion then collision), the collision (LBGK + Guo, Eq. 2, 3,
 //             7; or the incompressible / MRT models) and coalesced stores of all 19
 //             results into the other copy.
-// Solid nodes issue no copies. With FP32 storage a solid slot that shares a 32-byte sector
-// with a non-solid one gets its NaN stored again (the group's fill list), so that every
-// sector the step writes is written whole.
+// Solid nodes have no storage and issue no copies. A work group is also a storage group:
+// its nodes' values of direction i are one contiguous 256-value data block, so the
+// stores of a group write whole 32-byte sectors (DRAM never reads a sector back to merge
+// a partial write), and a gather reads the source node's padded lane from the neighbour
+// record of its tile (tlane plus the popcount of the tile's non-solid mask below the
+// source slot).
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
@@ -43,24 +46,20 @@ namespace lbm {
 // Measured and not kept: 8 CTAs of 128 threads (-25 %), 2 of 512 (-1 to -2 %), groups of
 // 16 tiles for the 4-byte formats (their larger neighbour staging pushes 4 CTAs past the
 // 196 KB carveout, leaving 28 KB of L1: -25 %).
-// FILL: the format has fill lists (full-sector writes, see fill_solid).
 template <int DT> struct StepCfg {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 4;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
-    static constexpr bool FILL = fill_sector_slots(DT) > 0;
 };
 template <> struct StepCfg<LBM_F32> {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 3;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
-    static constexpr bool FILL = fill_sector_slots(LBM_F32) > 0;
 };
 template <> struct StepCfg<LBM_F64> {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 2;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_F64;
-    static constexpr bool FILL = fill_sector_slots(LBM_F64) > 0;
 };
 static_assert(StepCfg<LBM_F32>::THREADS == GROUP_MAX_NODES && StepCfg<LBM_F64>::THREADS == GROUP_MAX_NODES_F64,
               "work groups and CTAs must agree");
@@ -112,13 +111,6 @@ __device__ __forceinline__ int4 group_header(const int4 h, const StepParams& p) 
                     h.z >= 0 && h.w >= 0 && h.w <= StepCfg<DT>::THREADS && (int64_t)h.z + h.w <= p.n_lanes;
     return check_ok(ok, CHECK_HEADER, h.x, p) ? h : make_int4(0, 0, 0, 0);
 }
-// The same for a group's fill range, which only launches with fill stages (FL) load.
-template <bool FL>
-__device__ __forceinline__ int2 fill_range(const int2 fr, const StepParams& p) {
-    if constexpr (!FL) return make_int2(0, 0);
-    const bool ok = fr.x >= 0 && fr.y >= 0 && (int64_t)fr.x + fr.y <= p.n_fill;
-    return check_ok(ok, CHECK_HEADER, fr.x, p) ? fr : make_int2(0, 0);
-}
 
 // Staged element: the stored element for F64/F32; for F16S the aligned 32-bit word that
 // holds the wanted half (cp.async moves at least 4 bytes), with the half picked later.
@@ -130,40 +122,36 @@ struct StepSmem {
     using E = typename Staged<DT>::E;
     using G = typename Store<DT>::R;
     int4 hdr[HDR_SLOTS];                                   // {t0, tiles, f0, nodes}
-    int2 frng[HDR_SLOTS];                                  // {first fill entry, fill entries}
-    int32_t nbr[META_SLOTS][StepCfg<DT>::MAX_TILES][NBR_STRIDE];
+    // neighbour records (index of each neighbour's first node) and the nodes' source ranks:
+    // read only when the group's gathers are issued, one iteration after they land, so two
+    // slots (those of the data ring)
+    int64_t rec[DATA_SLOTS][StepCfg<DT>::MAX_TILES][NBR_STRIDE];
+    uint4 rank[DATA_SLOTS][StepCfg<DT>::THREADS];
     uint32_t word[META_SLOTS][StepCfg<DT>::THREADS];
-    uint32_t fill[META_SLOTS][StepCfg<DT>::FILL ? StepCfg<DT>::THREADS : 1];   // fill entry THREADS - 1 - t
+    // F16S: bit i set when direction i's value is the upper half of its staged word
+    uint32_t odd[DATA_SLOTS][DT == LBM_F16S ? StepCfg<DT>::THREADS : 1];
     E data[DATA_SLOTS][Q][StepCfg<DT>::THREADS];
     // last, so that a launch without a per-node force field leaves it out of the dynamic
     // shared memory (the space goes to the L1 cache, which serves the 4-byte gathers)
     G gf[META_SLOTS][StepCfg<DT>::THREADS];
 };
 
-template <bool FILL>
-__device__ __forceinline__ void issue_hdr(int4* hdr, int2* frng, int64_t grp, int64_t n_groups,
-                                          const int4* __restrict__ groups, const int2* __restrict__ gfill_rng) {
+__device__ __forceinline__ void issue_hdr(int4* hdr, int64_t grp, int64_t n_groups, const int4* __restrict__ groups) {
     if (threadIdx.x == 0 && grp < n_groups) cp_async16(hdr, groups + grp);
-    if (FILL && threadIdx.x == 32 && grp < n_groups) cp_async8(frng, gfill_rng + grp);
 }
 
-// Neighbour records of the group's tiles, the words (and forces) of its nodes and the
-// first THREADS entries of its fill list.
-template <int DT, bool FL>
-__device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const int4 h, const int2 fr,
-                                           const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
-                                           const void* gfield_c, const uint32_t* __restrict__ gfill) {
+// Neighbour records of the group's tiles and the words (and forces) of its nodes.
+template <int DT>
+__device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, int rslot, const int4 h,
+                                           const int64_t* __restrict__ nrec, const uint32_t* __restrict__ fword,
+                                           const uint4* __restrict__ frank, const void* gfield_c) {
     const int t = threadIdx.x;
-    if constexpr (FL) {
-        const int j0 = StepCfg<DT>::THREADS - 1 - t;
-        if (j0 < fr.y) cp_async4(&sm.fill[mslot][t], gfill + fr.x + j0);
-    }
-    if (t < h.y * (NBR_STRIDE / 4)) {
-        const int lt = t / (NBR_STRIDE / 4), c = t % (NBR_STRIDE / 4);
-        cp_async16(&sm.nbr[mslot][lt][4 * c], nbr + (int64_t)(h.x + lt) * NBR_STRIDE + 4 * c);
-    }
+    constexpr int CH = NBR_STRIDE / 2;   // 16-byte chunks of a tile's records
+    for (int j = t; j < h.y * CH; j += StepCfg<DT>::THREADS)
+        cp_async16(&sm.rec[rslot][j / CH][2 * (j % CH)], nrec + ((int64_t)h.x + j / CH) * NBR_STRIDE + 2 * (j % CH));
     if (t < h.w) {
         cp_async4(&sm.word[mslot][t], fword + h.z + t);
+        cp_async16(&sm.rank[rslot][t], frank + h.z + t);
         if (gfield_c) {
             const typename Store<DT>::R* g = static_cast<const typename Store<DT>::R*>(gfield_c);
             if (DT == LBM_F64) cp_async8(&sm.gf[mslot][t], g + h.z + t);
@@ -175,54 +163,44 @@ __device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, const in
 }
 
 // Issue the 19 gathers of this thread's node (for F16S the aligned 32-bit word that holds
-// the wanted half).
+// the wanted half). sg: the group's storage group; the node's own padded lane is
+// 256 sg + t.
 template <int DT, int MODE>
-__device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int dslot, const int4 h,
+__device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, int64_t sg,
                                              const typename Store<DT>::T* __restrict__ A, const StepParams& p) {
-    using T = typename Store<DT>::T;
     const int t = threadIdx.x;
     const uint32_t w = sm.word[mslot][t];
     if (((w >> WORD_TYPE_SHIFT) & 3u) == LBM_SOLID) return;
     const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     if (!check_ok(lt < h.y, CHECK_OWN_TILE, (int64_t)h.z + t, p)) return;
     const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
-    const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
+    const int64_t own = sg * (Q * GROUP_LANES) + t;
+    const uint4 rk = sm.rank[dslot][t];
+    uint32_t odd = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         int64_t src;
-        if (MODE == STEP_RW) {
-            src = own + i * SLOTS + s;   // read/write only: the node's own values
+        if (MODE == STEP_RW || i == 0) {
+            src = own + i * GROUP_LANES;   // the rest population, or read/write only: the node's own values
         } else if ((w >> i) & 1) {
-            src = own + inv(i) * SLOTS + s;
+            src = own + inv(i) * GROUP_LANES;
         } else {
             const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
             const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
-            const int ss = (sx & 3) | ((sy & 3) << 2) | ((sz & 3) << 4);
-            const int32_t r = sm.nbr[mslot][lt][nb];
-            if (!check_ok(r >= 0 && r < p.n_tiles, CHECK_NEIGHBOUR, (int64_t)(h.x + lt) * NBR_STRIDE + nb, p)) continue;
-            src = (int64_t)r * (Q * SLOTS) + i * SLOTS + ss;
+            src = sm.rec[dslot][lt][nb] + i * GROUP_LANES + rank_of(rk, i);
+            if (!check_ok(src >= 0 && src < p.n_padded * Q, CHECK_NEIGHBOUR, ((int64_t)(h.x + lt) << 8) | (nb << 2), p))
+                continue;
         }
         if (DT == LBM_F64) {
             cp_async8(&sm.data[dslot][i][t], A + src);
         } else if (DT == LBM_F32) {
             cp_async4(&sm.data[dslot][i][t], A + src);
         } else {
-            cp_async4(&sm.data[dslot][i][t], reinterpret_cast<const char*>(A) + (src & ~(int64_t)1) * sizeof(T));
+            odd |= (uint32_t)(src & 1) << i;
+            cp_async4(&sm.data[dslot][i][t], A + (src & ~(int64_t)1));
         }
     }
-}
-
-// Directions with c_x != 0 (1, 3, 7-14).
-constexpr uint32_t CX_DIRS = (1u << 1) | (1u << 3) | (0xffu << 7);
-
-// F16S: which directions' values are the upper half of their staged 32-bit word. Data
-// blocks start at even element indices, so the half is the upper one when the source
-// slot is odd: a pulled source has slot parity (x - c_x) & 1, a bounced (or read/write)
-// source is the node's own slot, parity x & 1.
-template <int MODE>
-__device__ __forceinline__ uint32_t upper_halves(int s, uint32_t w) {
-    const uint32_t own = (s & 1) ? 0x7ffffu : 0u;
-    return MODE == STEP_RW ? own : own ^ (CX_DIRS & ~w);
+    if (DT == LBM_F16S) sm.odd[dslot][t] = odd;
 }
 
 // FP16 store of a node's 19 results h (FP32, unscaled) that keeps the node's mass and
@@ -240,7 +218,7 @@ __device__ __forceinline__ void store_f16_conserving(const float v[Q], __half* _
     float rx = 0.f, ry = 0.f, rz = 0.f, m = 0.f;
     auto put = [&](int i, float target) {
         const __half q = __float2half_rn(target * F16_SCALE);
-        dst[i * SLOTS] = q;
+        dst[i * GROUP_LANES] = q;
         const float r = v[i] - __half2float(q) * F16_INV_SCALE;
         m += r;
         if (cx(i)) rx += cx(i) > 0 ? r : -r;
@@ -260,7 +238,7 @@ __device__ __forceinline__ void store_f16_conserving(const float v[Q], __half* _
 }
 
 template <int DT, bool VAR, int MODE, bool GEN>
-__device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h,
+__device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, int64_t sg,
                                               typename Store<DT>::T* __restrict__ B, const StepParams& p,
                                               bool has_gf, uint32_t key) {
     using R = typename Store<DT>::R;
@@ -271,7 +249,7 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     if (type == LBM_SOLID) return;
     const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     R v[Q];
-    const uint32_t odd = DT == LBM_F16S ? upper_halves<MODE>(s, w) : 0u;
+    const uint32_t odd = DT == LBM_F16S ? sm.odd[DT == LBM_F16S ? dslot : 0][DT == LBM_F16S ? t : 0] : 0u;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         T e;
@@ -312,54 +290,30 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
         collide<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
     }
     if (!check_ok(lt < h.y, CHECK_OWN_TILE, (int64_t)h.z + t, p)) return;
-    const int64_t own = (int64_t)(h.x + lt) * (Q * SLOTS);
+    const int64_t own = sg * (Q * GROUP_LANES) + t;
     if constexpr (DT == LBM_F16S && VAR && MODE == STEP_FULL) {
         // stochastic rounding: two 16-bit dithers per hash of (key, node, pair)
         const uint32_t node = fmix32(key ^ (uint32_t)((h.x + lt) * SLOTS + s));
 #pragma unroll
         for (int i = 0; i < Q; i += 2) {
             const uint32_t r = fmix32(node + (uint32_t)(i >> 1) * 0x9e3779b9u);
-            B[own + i * SLOTS + s] = half_dithered(v[i] * F16_SCALE, r & 0xffffu);
-            if (i + 1 < Q) B[own + (i + 1) * SLOTS + s] = half_dithered(v[i + 1] * F16_SCALE, r >> 16);
+            B[own + i * GROUP_LANES] = half_dithered(v[i] * F16_SCALE, r & 0xffffu);
+            if (i + 1 < Q) B[own + (i + 1) * GROUP_LANES] = half_dithered(v[i + 1] * F16_SCALE, r >> 16);
         }
     } else if constexpr (DT == LBM_F16S && MODE == STEP_FULL) {
-        store_f16_conserving(v, B + own + s);
+        store_f16_conserving(v, B + own);
     } else {
 #pragma unroll
-        for (int i = 0; i < Q; i++) B[own + i * SLOTS + s] = to_store<DT>(v[i], i);
+        for (int i = 0; i < Q; i++) B[own + i * GROUP_LANES] = to_store<DT>(v[i], i);
     }
 }
 
-// NaN into the group's fill slots (solid or padding slots that share a 32-byte sector with
-// a non-solid slot), in all 19 data blocks. Together with the nodes' own stores every
-// sector the step writes is then written whole; a partly written sector would cost DRAM a
-// read of the sector to merge it. The slots hold NaN already, so nothing changes. Entry j
-// goes to thread THREADS - 1 - j, where the idle threads of a short group are; e0 is this
-// thread's first entry, staged in shared memory with the group's other metadata.
-template <int DT>
-__device__ __forceinline__ void fill_solid(typename Store<DT>::T* __restrict__ B, const int4 h, uint32_t e0,
-                                           const uint32_t* __restrict__ list, int nf, const StepParams& p) {
-    using T = typename Store<DT>::T;
-    const T nan = nan_value<DT>();
-    const int t0 = h.x;
-    int j = StepCfg<DT>::THREADS - 1 - (int)threadIdx.x;
-    for (uint32_t e = e0; j < nf; j += StepCfg<DT>::THREADS) {
-        if (j >= StepCfg<DT>::THREADS) e = __ldg(list + j);
-        if (!check_ok((int)(e >> 6) < h.y, CHECK_FILL, e, p)) continue;
-        T* q = B + (int64_t)(t0 + (int)(e >> 6)) * (Q * SLOTS) + (e & 63u);
-#pragma unroll
-        for (int i = 0; i < Q; i++) q[i * SLOTS] = nan;
-    }
-}
-
-// FL: this launch runs the fill stages (FP32 storage, an LBGK collision and a geometry with
-// fill slots; see use_fill).
-template <int DT, bool VAR, int MODE, bool GEN, bool FL>
+template <int DT, bool VAR, int MODE, bool GEN>
 __global__ void __launch_bounds__(StepCfg<DT>::THREADS, StepCfg<DT>::CTAS)
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
-       const int4* __restrict__ groups, const int32_t* __restrict__ nbr, const uint32_t* __restrict__ fword,
-       const void* __restrict__ gfield_c, const int2* __restrict__ gfill_rng, const uint32_t* __restrict__ gfill,
-       int64_t n_groups, StepParams p, const uint32_t* __restrict__ seed_in, uint32_t* __restrict__ seed_out) {
+       const int4* __restrict__ groups, const int64_t* __restrict__ nrec, const uint32_t* __restrict__ fword,
+       const uint4* __restrict__ frank, const void* __restrict__ gfield_c, int64_t n_groups, StepParams p, const uint32_t* __restrict__ seed_in,
+       uint32_t* __restrict__ seed_out) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     StepSmem<DT>& sm = *reinterpret_cast<StepSmem<DT>*>(smem_raw);
     const int64_t G = gridDim.x;
@@ -375,48 +329,41 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     if (g0 >= n_groups) return;
     const bool has_gf = gfield_c != nullptr;
     // prologue: headers of groups 0..2, meta of groups 0..1, gathers of group 0
-    issue_hdr<FL>(&sm.hdr[0], &sm.frng[0], g0, n_groups, groups, gfill_rng);
+    issue_hdr(&sm.hdr[0], g0, n_groups, groups);
     cp_async_commit();
-    issue_hdr<FL>(&sm.hdr[1], &sm.frng[1], g0 + G, n_groups, groups, gfill_rng);
+    issue_hdr(&sm.hdr[1], g0 + G, n_groups, groups);
     cp_async_commit();
-    issue_hdr<FL>(&sm.hdr[2], &sm.frng[2], g0 + 2 * G, n_groups, groups, gfill_rng);
+    issue_hdr(&sm.hdr[2], g0 + 2 * G, n_groups, groups);
     cp_async_commit();
     cp_async_wait<0>();
     __syncthreads();
-    issue_meta<DT, FL>(sm, 0, group_header<DT>(sm.hdr[0], p), fill_range<FL>(sm.frng[0], p), nbr, fword, gfield_c,
-                       gfill);
+    issue_meta<DT>(sm, 0, 0, group_header<DT>(sm.hdr[0], p), nrec, fword, frank, gfield_c);
     cp_async_commit();
-    if (g0 + G < n_groups)
-        issue_meta<DT, FL>(sm, 1, group_header<DT>(sm.hdr[1], p), fill_range<FL>(sm.frng[1], p), nbr, fword, gfield_c,
-                           gfill);
+    if (g0 + G < n_groups) issue_meta<DT>(sm, 1, 1, group_header<DT>(sm.hdr[1], p), nrec, fword, frank, gfield_c);
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    issue_gather<DT, MODE>(sm, 0, 0, group_header<DT>(sm.hdr[0], p), A, p);
+    issue_gather<DT, MODE>(sm, 0, 0, group_header<DT>(sm.hdr[0], p), p.sg0 + g0, A, p);
     cp_async_commit();
     int it = 0;
     for (int64_t g = g0; g < n_groups; g += G, it++) {
         // pending: header(g + 2G) [done], meta(g + G), gather(g)
         cp_async_wait<1>();
         __syncthreads();   // header(g + 2G), meta(g + G) visible; iteration it - 1 finished
-        issue_hdr<FL>(&sm.hdr[(it + 3) & 3], &sm.frng[(it + 3) & 3], g + 3 * G, n_groups, groups, gfill_rng);
+        issue_hdr(&sm.hdr[(it + 3) & 3], g + 3 * G, n_groups, groups);
         cp_async_commit();
         if (g + 2 * G < n_groups)
-            issue_meta<DT, FL>(sm, (it + 2) % META_SLOTS, group_header<DT>(sm.hdr[(it + 2) & 3], p),
-                               fill_range<FL>(sm.frng[(it + 2) & 3], p), nbr, fword, gfield_c, gfill);
+            issue_meta<DT>(sm, (it + 2) % META_SLOTS, it & 1, group_header<DT>(sm.hdr[(it + 2) & 3], p), nrec, fword,
+                           frank, gfield_c);
         cp_async_commit();
         if (g + G < n_groups)
             issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, group_header<DT>(sm.hdr[(it + 1) & 3], p),
-                                   A, p);
+                                   p.sg0 + g + G, A, p);
         cp_async_commit();
         // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
         cp_async_wait<3>();
         const int4 h = group_header<DT>(sm.hdr[it & 3], p);
-        compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, h, B, p, has_gf, key);
-        if constexpr (FL) {
-            const int2 fr = fill_range<FL>(sm.frng[it & 3], p);
-            fill_solid<DT>(B, h, sm.fill[it % META_SLOTS][threadIdx.x], gfill + fr.x, fr.y, p);
-        }
+        compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, h, p.sg0 + g, B, p, has_gf, key);
     }
     cp_async_wait<0>();
 }
@@ -434,7 +381,7 @@ static size_t step_smem(bool with_gf) {
 // (cp.async.ca). Left to itself the driver picks the carveout for the highest occupancy:
 // a light kernel (the calibration kinds) would fit a fifth CTA and keep 28 KB of L1
 // instead of 60 KB, and run 25 % slower.
-template <int DT, bool VAR, int MODE, bool GEN, bool FL>
+template <int DT, bool VAR, int MODE, bool GEN>
 static int step_grid(int64_t n_groups, bool with_gf) {
     static int per_sm[2] = {-1, -1}, n_sm = 0;
     int& ps = per_sm[with_gf ? 1 : 0];
@@ -444,58 +391,38 @@ static int step_grid(int64_t n_groups, bool with_gf) {
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, FL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
         if (smem_sm > 0) {
             const double need = (double)StepCfg<DT>::CTAS * (double)(sizeof(StepSmem<DT>) + (size_t)reserved);
             const int pct = std::min(100, std::max(1, (int)std::ceil(100.0 * need / smem_sm)));
-            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, FL>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
         }
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN, FL>, StepCfg<DT>::THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN>, StepCfg<DT>::THREADS,
                                                       step_smem<DT>(with_gf));
         ps = std::max(1, std::min(ps, StepCfg<DT>::CTAS));
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)ps * n_sm));
 }
 
-template <int DT, bool VAR, int MODE, bool GEN, bool FL>
-static cudaError_t launch_step_fl(lbm_ctx* c, const void* A, void* B) {
+template <int DT, bool VAR, int MODE, bool GEN>
+static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
     const bool with_gf = c->gfield != nullptr;
-    const int grid = step_grid<DT, VAR, MODE, GEN, FL>(c->n_groups, with_gf);
+    const int grid = step_grid<DT, VAR, MODE, GEN>(c->n_groups, with_gf);
     // the copy read decides which counter is read and which is advanced
     const int from = A == c->f[0] ? 0 : 1;
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
-    k_step<DT, VAR, MODE, GEN, FL><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
-        (const T*)A, (T*)B, c->groups, c->nbr, c->fword, c->gfield ? c->gfield_c : nullptr, c->gfill_rng, c->gfill,
-        c->n_groups, c->p, seed_in, seed_out);
+    k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
+        (const T*)A, (T*)B, c->groups, c->nrec, c->fword, c->frank, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
+        seed_in, seed_out);
     return cudaGetLastError();
-}
-
-// The fill stages run only where they pay: a geometry with fill slots (not dense) and an
-// LBGK collision. The MRT collision is bound by instruction issue like the FP64 and FP16
-// steps, and its FP32 step ran 6 % slower with them.
-static bool use_fill(const lbm_ctx* c) { return c->n_fill > 0 && c->p.coll == LBM_COLL_BGK; }
-
-template <int DT, bool VAR, int MODE, bool GEN>
-static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
-    if constexpr (StepCfg<DT>::FILL) {
-        if (use_fill(c)) return launch_step_fl<DT, VAR, MODE, GEN, true>(c, A, B);
-    }
-    return launch_step_fl<DT, VAR, MODE, GEN, false>(c, A, B);
 }
 
 template <int DT, bool VAR, bool GEN>
 static void prepare_dt(lbm_ctx* c) {
-    const bool with_gf = c->gfield != nullptr;
-    if constexpr (StepCfg<DT>::FILL) {
-        if (use_fill(c)) {
-            step_grid<DT, VAR, STEP_FULL, GEN, true>(1, with_gf);
-            return;
-        }
-    }
-    step_grid<DT, VAR, STEP_FULL, GEN, false>(1, with_gf);
+    step_grid<DT, VAR, STEP_FULL, GEN>(1, c->gfield != nullptr);
 }
 
 template <int MODE, bool GEN>

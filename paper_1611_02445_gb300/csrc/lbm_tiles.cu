@@ -234,19 +234,21 @@ cudaError_t launch_node_words(lbm_ctx* c) {
 }
 
 // ----------------------------------------------------------------------------------
-// Equilibrium initial state f = f^eq(rho0, u0) (Eq. 3) in both copies; solid slots hold
-// NaN so that any read of one would show in the results.
+// Equilibrium initial state f = f^eq(rho0, u0) (Eq. 3) of every non-solid node, in both
+// copies.
 template <int DT>
 __global__ void k_init(typename Store<DT>::T* __restrict__ f0, typename Store<DT>::T* __restrict__ f1,
-                       const uint64_t* __restrict__ smask, int64_t n_tiles, double rho0, double ux,
-                       double uy, double uz, int eq) {
+                       const uint64_t* __restrict__ smask, const int32_t* __restrict__ tlane, int64_t n_tiles,
+                       double rho0, double ux, double uy, double uz, int eq) {
     using T = typename Store<DT>::T;
     const int64_t n = n_tiles * SLOTS;
     for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = idx >> 6;
         const int s = (int)(idx & 63);
-        const bool solid = (smask[k] >> s) & 1;
+        const uint64_t sm = smask[k];
+        if ((sm >> s) & 1) continue;   // solid slots have no storage
+        const uint32_t P = node_lane((uint32_t)tlane[k], sm, s);
         const double uu = ux * ux + uy * uy + uz * uz;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
@@ -254,63 +256,95 @@ __global__ void k_init(typename Store<DT>::T* __restrict__ f0, typename Store<DT
             // Eq. 3, or Eq. 4 for the incompressible model
             const double fe = eq == LBM_EQ_INCOMPR ? wgt(i) * (rho0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu)
                                                    : wgt(i) * rho0 * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu);
-            const T v = solid ? nan_value<DT>() : from_f64<DT>(fe, i);
-            f0[(k * Q + i) * SLOTS + s] = v;
-            f1[(k * Q + i) * SLOTS + s] = v;
+            const T v = from_f64<DT>(fe, i);
+            f0[data_index(P, i)] = v;
+            f1[data_index(P, i)] = v;
         }
     }
 }
 
-// The per-lane lists of the step's work groups (fword, fidx and, with fill lists, gfill),
-// from what the host decided per tile while forming the groups: the non-solid nodes of
-// tile k take lanes lane0[k], lane0[k] + 1, ... in slot order, lt[k] is the tile's index
-// within its group, and its fill entries start at fill0[k]. One CTA of 64 threads per tile,
-// one thread per slot; a slot's rank is the popcount of the tile's masks below it.
+// The per-lane lists of the step's work groups (fword, fidx), from what the host decided
+// per tile while forming the groups: the non-solid nodes of tile k take lanes lane0[k],
+// lane0[k] + 1, ... in slot order, and lt[k] is the tile's index within its group. One CTA
+// of 64 threads per tile, one thread per slot; a slot's rank is the popcount of the
+// tile's non-solid mask below it.
 __global__ void k_lane_lists(const uint32_t* __restrict__ nword, const uint64_t* __restrict__ smask,
-                             const int64_t* __restrict__ lane0, const uint8_t* __restrict__ lt,
-                             const int64_t* __restrict__ fill0, int sector, int64_t k0, int64_t k1,
-                             uint32_t* __restrict__ fword, uint32_t* __restrict__ fidx, uint32_t* __restrict__ gfill) {
+                             const int32_t* __restrict__ nbr, const int64_t* __restrict__ lane0,
+                             const uint8_t* __restrict__ lt, int64_t k0, int64_t k1, uint32_t* __restrict__ fword,
+                             uint32_t* __restrict__ fidx, uint4* __restrict__ frank) {
     const int s = threadIdx.x;
+    const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
     const uint64_t below = (1ull << s) - 1ull;   // s < 64
     for (int64_t k = k0 + blockIdx.x; k < k1; k += gridDim.x) {
         const uint64_t sm = smask[k];
         const uint32_t l = lt[k - k0];
         if (!((sm >> s) & 1ull)) {
             const int64_t idx = lane0[k - k0] + __popcll(~sm & below);
-            fword[idx] = nword[k * SLOTS + s] | (l << WORD_LT_SHIFT) | ((uint32_t)s << WORD_SLOT_SHIFT);
+            const uint32_t w = nword[k * SLOTS + s];
+            fword[idx] = w | (l << WORD_LT_SHIFT) | ((uint32_t)s << WORD_SLOT_SHIFT);
             fidx[idx] = (uint32_t)(k * SLOTS + s);
-        } else if (sector > 0) {
-            const uint64_t fm = fill_mask(sm, sector);
-            if ((fm >> s) & 1ull) gfill[fill0[k - k0] + __popcll(fm & below)] = l * SLOTS + (uint32_t)s;
+            uint32_t r[4] = {0u, 0u, 0u, 0u};
+            for (int i = 1; i < Q; i++) {
+                if ((w >> i) & 1u) continue;   // bounced: no source in another slot
+                const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
+                const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
+                const int ss = (sx & 3) | ((sy & 3) << 2) | ((sz & 3) << 4);
+                const int32_t nk = nbr[k * NBR_STRIDE + nb];   // >= 0: the link does not bounce
+                const uint32_t rank = (uint32_t)__popcll(~smask[nk] & ((1ull << ss) - 1ull));
+                r[(i - 1) / 5] |= rank << (6 * ((i - 1) % 5));
+            }
+            frank[idx] = make_uint4(r[0], r[1], r[2], r[3]);
         }
     }
 }
 
-cudaError_t launch_lane_lists(lbm_ctx* c, const int64_t* lane0, const uint8_t* lt, const int64_t* fill0, int sector) {
+cudaError_t launch_lane_lists(lbm_ctx* c, const int64_t* lane0, const uint8_t* lt) {
     const int64_t n = c->own_k1 - c->own_k0;
     if (n <= 0) return cudaSuccess;
     k_lane_lists<<<(unsigned)std::min<int64_t>(n, 1 << 20), SLOTS, 0, c->stream>>>(
-        c->nword, c->smask, lane0, lt, fill0, sector, c->own_k0, c->own_k1, c->fword, c->fidx, c->gfill);
+        c->nword, c->smask, c->nbr, lane0, lt, c->own_k0, c->own_k1, c->fword, c->fidx, c->frank);
     return cudaGetLastError();
+}
+
+// The step's neighbour records: for each kept tile and each of its 27 neighbourhood
+// entries, the index of the neighbour's first non-solid node in data block 0 of a copy
+// (zero for a dropped or out-of-box neighbour, and in the padding entry). One thread per
+// record.
+__global__ void k_node_records(const int32_t* __restrict__ nbr, const int32_t* __restrict__ tlane, int64_t n_tiles,
+                               int64_t* __restrict__ nrec) {
+    const int64_t n = n_tiles * NBR_STRIDE;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int e = (int)(idx % NBR_STRIDE);
+        const int32_t r = e < NBR ? nbr[idx] : -1;
+        nrec[idx] = r >= 0 && r < n_tiles ? data_index((uint32_t)tlane[r], 0) : 0;
+    }
 }
 
 static unsigned grid_for(int64_t n, int threads) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 152 * 32));
 }
 
+cudaError_t launch_node_records(lbm_ctx* c) {
+    if (c->n_tiles <= 0) return cudaSuccess;
+    k_node_records<<<grid_for(c->n_tiles * NBR_STRIDE, 256), 256, 0, c->stream>>>(c->nbr, c->tlane, c->n_tiles,
+                                                                                 c->nrec);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_init(lbm_ctx* c, double rho0, const double u0[3]) {
     const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
     switch (c->dtype) {
         case LBM_F64:
-            k_init<LBM_F64><<<g, 256, 0, c->stream>>>((double*)c->f[0], (double*)c->f[1], c->smask,
+            k_init<LBM_F64><<<g, 256, 0, c->stream>>>((double*)c->f[0], (double*)c->f[1], c->smask, c->tlane,
                                                       c->n_tiles, rho0, u0[0], u0[1], u0[2], c->p.eq);
             break;
         case LBM_F32:
-            k_init<LBM_F32><<<g, 256, 0, c->stream>>>((float*)c->f[0], (float*)c->f[1], c->smask,
+            k_init<LBM_F32><<<g, 256, 0, c->stream>>>((float*)c->f[0], (float*)c->f[1], c->smask, c->tlane,
                                                       c->n_tiles, rho0, u0[0], u0[1], u0[2], c->p.eq);
             break;
         default:
-            k_init<LBM_F16S><<<g, 256, 0, c->stream>>>((__half*)c->f[0], (__half*)c->f[1], c->smask,
+            k_init<LBM_F16S><<<g, 256, 0, c->stream>>>((__half*)c->f[0], (__half*)c->f[1], c->smask, c->tlane,
                                                        c->n_tiles, rho0, u0[0], u0[1], u0[2], c->p.eq);
     }
     return cudaGetLastError();
@@ -336,8 +370,7 @@ __device__ __forceinline__ float red_add(float a, float b, float& err) {
 }
 
 template <int DT>
-__device__ __forceinline__ void node_moments(const typename Store<DT>::T* __restrict__ f, int64_t k, int s,
-                                             double m[4]) {
+__device__ __forceinline__ void node_moments(const typename Store<DT>::T* __restrict__ f, uint32_t P, double m[4]) {
     if constexpr (DT == LBM_F64) {
         // exact fixed-point sums; the conversion maps NaN and Inf to finite integers, so
         // a non-finite population is tested for on its exponent bits and makes every
@@ -346,7 +379,7 @@ __device__ __forceinline__ void node_moments(const typename Store<DT>::T* __rest
         uint64_t nonfinite = 0;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const double v = f[(k * Q + i) * SLOTS + s];
+            const double v = f[data_index(P, i)];
             const uint64_t b = (uint64_t)__double_as_longlong(v);
             nonfinite |= (~b & 0x7ff0000000000000ull) == 0 ? 1ull : 0ull;
             const int64_t q = fix_from_double(v);
@@ -365,7 +398,7 @@ __device__ __forceinline__ void node_moments(const typename Store<DT>::T* __rest
         float r = 0.f, jx = 0.f, jy = 0.f, jz = 0.f, er = 0.f, ex = 0.f, ey = 0.f, ez = 0.f;
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const float h = to_arith<DT>(f[(k * Q + i) * SLOTS + s], i);
+            const float h = to_arith<DT>(f[data_index(P, i)], i);
             r = red_add(r, h, er);
             if (cx(i)) jx = red_add(jx, cx(i) > 0 ? h : -h, ex);
             if (cy(i)) jy = red_add(jy, cy(i) > 0 ? h : -h, ey);
@@ -381,6 +414,7 @@ __device__ __forceinline__ void node_moments(const typename Store<DT>::T* __rest
 template <int DT>
 __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Store<DT>::T* __restrict__ f,
                                                         const uint64_t* __restrict__ smask,
+                                                        const int32_t* __restrict__ tlane,
                                                         const void* __restrict__ gfield, int64_t n_tiles,
                                                         StepParams p, double* __restrict__ partials) {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
@@ -389,9 +423,10 @@ __global__ void __launch_bounds__(RED_THREADS) k_reduce(const typename Store<DT>
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = idx >> 6;
         const int s = (int)(idx & 63);
-        if ((smask[k] >> s) & 1) continue;
+        const uint64_t sm = smask[k];
+        if ((sm >> s) & 1) continue;
         double m[4];
-        node_moments<DT>(f, k, s, m);
+        node_moments<DT>(f, node_lane((uint32_t)tlane[k], sm, s), m);
         const double Fx = gfield ? gfield_at<DT>(gfield, idx) : p.g[0];
         acc[0] += m[0];
         acc[1] += m[1] - 0.5 * Fx;
@@ -440,6 +475,7 @@ int reduce_blocks(int64_t n_tiles) {
 struct OwnTiles {
     const void* f;
     const uint64_t* smask;
+    const int32_t* tlane;
     const uint32_t* non_empty;
     const void* gfield;
     int64_t n;
@@ -447,8 +483,7 @@ struct OwnTiles {
 static OwnTiles own_tiles(const lbm_ctx* c) {
     const int64_t k0 = c->own_k0;
     const size_t gsize = c->dtype == LBM_F64 ? 8 : 4;
-    return {static_cast<const char*>(c->f[c->cur]) + (size_t)k0 * Q * SLOTS * dtype_size(c->dtype), c->smask + k0,
-            c->non_empty + k0, c->gfield ? static_cast<const char*>(c->gfield) + (size_t)k0 * SLOTS * gsize : nullptr,
+    return {c->f[c->cur], c->smask + k0, c->tlane + k0, c->non_empty + k0, c->gfield ? static_cast<const char*>(c->gfield) + (size_t)k0 * SLOTS * gsize : nullptr,
             c->own_k1 - k0};
 }
 
@@ -457,15 +492,15 @@ cudaError_t launch_reduce(lbm_ctx* c, double* d_out) {
     const OwnTiles o = own_tiles(c);
     switch (c->dtype) {
         case LBM_F64:
-            k_reduce<LBM_F64><<<nb, RED_THREADS, 0, c->stream>>>((const double*)o.f, o.smask, o.gfield, o.n, c->p,
+            k_reduce<LBM_F64><<<nb, RED_THREADS, 0, c->stream>>>((const double*)o.f, o.smask, o.tlane, o.gfield, o.n, c->p,
                                                                  c->partials);
             break;
         case LBM_F32:
-            k_reduce<LBM_F32><<<nb, RED_THREADS, 0, c->stream>>>((const float*)o.f, o.smask, o.gfield, o.n, c->p,
+            k_reduce<LBM_F32><<<nb, RED_THREADS, 0, c->stream>>>((const float*)o.f, o.smask, o.tlane, o.gfield, o.n, c->p,
                                                                  c->partials);
             break;
         default:
-            k_reduce<LBM_F16S><<<nb, RED_THREADS, 0, c->stream>>>((const __half*)o.f, o.smask, o.gfield, o.n, c->p,
+            k_reduce<LBM_F16S><<<nb, RED_THREADS, 0, c->stream>>>((const __half*)o.f, o.smask, o.tlane, o.gfield, o.n, c->p,
                                                                   c->partials);
     }
     k_reduce_final<<<1, RED_THREADS, 0, c->stream>>>(c->partials, nb, d_out);
@@ -478,7 +513,8 @@ cudaError_t launch_reduce(lbm_ctx* c, double* d_out) {
 // model), into dense arrays (already zeroed by the caller).
 template <int DT, typename O>
 __global__ void k_macro(const typename Store<DT>::T* __restrict__ f, const uint64_t* __restrict__ smask,
-                        const uint32_t* __restrict__ non_empty, const void* __restrict__ gfield,
+                        const int32_t* __restrict__ tlane, const uint32_t* __restrict__ non_empty,
+                        const void* __restrict__ gfield,
                         int64_t n_tiles, int nx, int ny, int nz, int Tx, int Ty, StepParams p,
                         O* __restrict__ rho, O* __restrict__ u) {
     const int64_t n = n_tiles * SLOTS;
@@ -487,14 +523,15 @@ __global__ void k_macro(const typename Store<DT>::T* __restrict__ f, const uint6
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = idx >> 6;
         const int s = (int)(idx & 63);
-        if ((smask[k] >> s) & 1) continue;
+        const uint64_t sm = smask[k];
+        if ((sm >> s) & 1) continue;
         const uint32_t t = non_empty[k];
         const int x = TILE * (int)(t % (uint32_t)Tx) + (s & 3);
         const int y = TILE * (int)((t / (uint32_t)Tx) % (uint32_t)Ty) + ((s >> 2) & 3);
         const int z = TILE * (int)(t / ((uint32_t)Tx * (uint32_t)Ty)) + (s >> 4);
         const int64_t node = x + (int64_t)nx * (y + (int64_t)ny * z);
         double m[4];
-        node_moments<DT>(f, k, s, m);
+        node_moments<DT>(f, node_lane((uint32_t)tlane[k], sm, s), m);
         const double r = m[0], jx = m[1], jy = m[2], jz = m[3];
         const double Fx = gfield ? gfield_at<DT>(gfield, idx) : p.g[0];
         rho[node] = (O)r;
@@ -516,7 +553,7 @@ static void macro_dispatch(lbm_ctx* c, O* rho, O* u) {
     const OwnTiles o = own_tiles(c);
     const unsigned g = grid_for(o.n * SLOTS, 256);
 #define LBM_MACRO(DT, TT)                                                                                 \
-    k_macro<DT, O><<<g, 256, 0, c->stream>>>((const TT*)o.f, o.smask, o.non_empty, o.gfield, o.n, c->nx, c->ny, \
+    k_macro<DT, O><<<g, 256, 0, c->stream>>>((const TT*)o.f, o.smask, o.tlane, o.non_empty, o.gfield, o.n, c->nx, c->ny, \
                                              c->nz, c->Tx, c->Ty, c->p, rho, u)
     if (c->dtype == LBM_F64) LBM_MACRO(LBM_F64, double);
     else if (c->dtype == LBM_F32) LBM_MACRO(LBM_F32, float);
@@ -535,7 +572,7 @@ cudaError_t launch_macroscopic(lbm_ctx* c, void* rho, void* u, int out_f64) {
 // Box export: out[i][bz][by][bx] in FP64; NaN for solid, dropped or outside nodes.
 template <int DT>
 __global__ void k_get_box(const typename Store<DT>::T* __restrict__ f, const int32_t* __restrict__ tile_map,
-                          const uint64_t* __restrict__ smask, int nx, int ny, int nz, int Tx, int Ty,
+                          const uint64_t* __restrict__ smask, const int32_t* __restrict__ tlane, int nx, int ny, int nz, int Tx, int Ty,
                           unsigned periodic, int x0, int y0, int z0, int bx, int by, int bz,
                           double* __restrict__ out) {
     const int64_t B = (int64_t)bx * by * bz;
@@ -551,15 +588,16 @@ __global__ void k_get_box(const typename Store<DT>::T* __restrict__ f, const int
             }
         }
         int64_t k = -1;
-        int s = 0;
+        uint32_t P = 0;
         if (inside) {
             k = tile_map[p[0] / TILE + (int64_t)Tx * (p[1] / TILE + (int64_t)Ty * (p[2] / TILE))];
-            s = (p[0] & 3) + 4 * (p[1] & 3) + 16 * (p[2] & 3);
+            const int s = (p[0] & 3) + 4 * (p[1] & 3) + 16 * (p[2] & 3);
             if (k >= 0 && ((smask[k] >> s) & 1)) k = -1;
+            if (k >= 0) P = node_lane((uint32_t)tlane[k], smask[k], s);
         }
 #pragma unroll
         for (int i = 0; i < Q; i++)
-            out[i * B + b] = k >= 0 ? to_f64<DT>(f[(k * Q + i) * SLOTS + s], i) : __longlong_as_double(0x7ff8000000000000ll);
+            out[i * B + b] = k >= 0 ? to_f64<DT>(f[data_index(P, i)], i) : __longlong_as_double(0x7ff8000000000000ll);
     }
 }
 
@@ -567,7 +605,7 @@ cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, i
     const unsigned g = grid_for((int64_t)bx * by * bz, 256);
     const void* A = c->f[c->cur];
 #define LBM_BOX(DT, TT)                                                                                   \
-    k_get_box<DT><<<g, 256, 0, c->stream>>>((const TT*)A, c->tile_map, c->smask, c->nx, c->ny, c->nz, c->Tx, \
+    k_get_box<DT><<<g, 256, 0, c->stream>>>((const TT*)A, c->tile_map, c->smask, c->tlane, c->nx, c->ny, c->nz, c->Tx, \
                                             c->Ty, c->periodic, x0, y0, z0, bx, by, bz, d_out)
     if (c->dtype == LBM_F64) LBM_BOX(LBM_F64, double);
     else if (c->dtype == LBM_F32) LBM_BOX(LBM_F32, float);
@@ -576,12 +614,12 @@ cudaError_t launch_get_box(lbm_ctx* c, int x0, int y0, int z0, int bx, int by, i
     return cudaGetLastError();
 }
 
-// Dense FP64 import into both copies; solid and padding slots get NaN.
+// Dense FP64 import of the non-solid nodes into both copies.
 template <int DT>
 __global__ void k_set_dense(typename Store<DT>::T* __restrict__ f0, typename Store<DT>::T* __restrict__ f1,
                             const double* __restrict__ dense, const uint64_t* __restrict__ smask,
-                            const uint32_t* __restrict__ non_empty, int64_t n_tiles, int nx, int ny, int nz,
-                            int Tx, int Ty) {
+                            const int32_t* __restrict__ tlane, const uint32_t* __restrict__ non_empty,
+                            int64_t n_tiles, int nx, int ny, int nz, int Tx, int Ty) {
     using T = typename Store<DT>::T;
     const int64_t n = n_tiles * SLOTS;
     const int64_t N = (int64_t)nx * ny * nz;
@@ -589,17 +627,19 @@ __global__ void k_set_dense(typename Store<DT>::T* __restrict__ f0, typename Sto
          idx += (int64_t)gridDim.x * blockDim.x) {
         const int64_t k = idx >> 6;
         const int s = (int)(idx & 63);
-        const bool solid = (smask[k] >> s) & 1;
+        const uint64_t sm = smask[k];
+        if ((sm >> s) & 1) continue;   // solid slots have no storage
+        const uint32_t P = node_lane((uint32_t)tlane[k], sm, s);
         const uint32_t t = non_empty[k];
         const int x = TILE * (int)(t % (uint32_t)Tx) + (s & 3);
         const int y = TILE * (int)((t / (uint32_t)Tx) % (uint32_t)Ty) + ((s >> 2) & 3);
         const int z = TILE * (int)(t / ((uint32_t)Tx * (uint32_t)Ty)) + (s >> 4);
-        const int64_t node = solid ? 0 : x + (int64_t)nx * (y + (int64_t)ny * z);
+        const int64_t node = x + (int64_t)nx * (y + (int64_t)ny * z);
 #pragma unroll
         for (int i = 0; i < Q; i++) {
-            const T v = solid ? nan_value<DT>() : from_f64<DT>(dense[i * N + node], i);
-            f0[(k * Q + i) * SLOTS + s] = v;
-            f1[(k * Q + i) * SLOTS + s] = v;
+            const T v = from_f64<DT>(dense[i * N + node], i);
+            f0[data_index(P, i)] = v;
+            f1[data_index(P, i)] = v;
         }
     }
 }
@@ -608,7 +648,7 @@ cudaError_t launch_set_dense(lbm_ctx* c, const double* d_dense) {
     const unsigned g = grid_for(c->n_tiles * SLOTS, 256);
 #define LBM_SET(DT, TT)                                                                                   \
     k_set_dense<DT><<<g, 256, 0, c->stream>>>((TT*)c->f[c->cur], (TT*)c->f[1 - c->cur], d_dense, c->smask, \
-                                              c->non_empty, c->n_tiles, c->nx, c->ny, c->nz, c->Tx, c->Ty)
+                                              c->tlane, c->non_empty, c->n_tiles, c->nx, c->ny, c->nz, c->Tx, c->Ty)
     if (c->dtype == LBM_F64) LBM_SET(LBM_F64, double);
     else if (c->dtype == LBM_F32) LBM_SET(LBM_F32, float);
     else LBM_SET(LBM_F16S, __half);
@@ -700,40 +740,59 @@ cudaError_t launch_gfield(lbm_ctx* c, const double* d_dense) {
 // Halo of a slab context (lbm_create_slab): the populations that cross the cut between
 // two slabs. A node of the lowest own plane pulls from the plane below through the five
 // directions with c_z = +1, one of the highest own plane from the plane above through
-// the five with c_z = -1. Pack copies the own boundary plane's blocks of the directions
+// the five with c_z = -1. Pack copies the own boundary plane's values of the directions
 // its neighbour reads (side 0: the lowest plane, for the slab below, c_z = -1; side 1:
 // the highest, for the slab above, c_z = +1) from the current copy into buf, laid out
-// [direction][tile][64]; unpack copies buf into the ghost plane on that side (side 0:
-// c_z = +1, side 1: c_z = -1). Both are strided device copies of whole 64-value blocks.
+// [direction][tile][64] with NaN in the solid slots; unpack copies the non-solid slots of
+// buf into the ghost plane on that side (side 0: c_z = +1, side 1: c_z = -1). Both slabs
+// hold the plane's tiles in the same order with the same masks, so the layout agrees.
+struct HaloDirs {
+    int d[5];
+};
+
+template <int DT>
+__global__ void k_halo(typename Store<DT>::T* __restrict__ f, const uint64_t* __restrict__ smask,
+                       const int32_t* __restrict__ tlane, int64_t n_tiles, HaloDirs dirs, int pack,
+                       typename Store<DT>::T* __restrict__ buf) {
+    const int64_t n = n_tiles * SLOTS;
+    for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < n;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = idx >> 6;
+        const int s = (int)(idx & 63);
+        const uint64_t sm = smask[k];
+        const bool solid = (sm >> s) & 1;
+        const uint32_t P = solid ? 0u : node_lane((uint32_t)tlane[k], sm, s);
+#pragma unroll
+        for (int d = 0; d < 5; d++) {
+            if (pack) buf[d * n + idx] = solid ? nan_value<DT>() : f[data_index(P, dirs.d[d])];
+            else if (!solid) f[data_index(P, dirs.d[d])] = buf[d * n + idx];
+        }
+    }
+}
+
 cudaError_t launch_halo(lbm_ctx* c, int side, int pack, void* buf) {
-    static const int kDown[5] = {6, 12, 14, 16, 18};   // c_z = -1
-    static const int kUp[5] = {5, 11, 13, 15, 17};     // c_z = +1
-    const size_t es = dtype_size(c->dtype);
-    const size_t block = SLOTS * es, pitch = (size_t)Q * SLOTS * es;
+    HaloDirs down = {{6, 12, 14, 16, 18}};   // c_z = -1
+    HaloDirs up = {{5, 11, 13, 15, 17}};     // c_z = +1
     int64_t k0, n;
-    const int* dirs;
+    HaloDirs dirs;
     if (pack) {
         k0 = side == 0 ? c->own_k0 : c->own_k1 - c->bnd_hi;
         n = side == 0 ? c->bnd_lo : c->bnd_hi;
-        dirs = side == 0 ? kDown : kUp;
+        dirs = side == 0 ? down : up;
     } else {
         k0 = side == 0 ? 0 : c->own_k1;
         n = side == 0 ? c->own_k0 : c->n_tiles - c->own_k1;
-        dirs = side == 0 ? kUp : kDown;
+        dirs = side == 0 ? up : down;
     }
     if (n == 0) return cudaSuccess;
-    char* f = static_cast<char*>(c->f[c->cur]) + (size_t)k0 * pitch;
-    char* b = static_cast<char*>(buf);
-    for (int d = 0; d < 5; d++) {
-        char* tiles = f + (size_t)dirs[d] * block;
-        char* part = b + (size_t)d * n * block;
-        const cudaError_t e = pack ? cudaMemcpy2DAsync(part, block, tiles, pitch, block, (size_t)n,
-                                                       cudaMemcpyDeviceToDevice, c->stream)
-                                   : cudaMemcpy2DAsync(tiles, pitch, part, block, block, (size_t)n,
-                                                       cudaMemcpyDeviceToDevice, c->stream);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const unsigned g = grid_for(n * SLOTS, 256);
+#define LBM_HALO(DT, TT)                                                                                     \
+    k_halo<DT><<<g, 256, 0, c->stream>>>((TT*)c->f[c->cur], c->smask + k0, c->tlane + k0, n, dirs, pack, (TT*)buf)
+    if (c->dtype == LBM_F64) LBM_HALO(LBM_F64, double);
+    else if (c->dtype == LBM_F32) LBM_HALO(LBM_F32, float);
+    else LBM_HALO(LBM_F16S, __half);
+#undef LBM_HALO
+    return cudaGetLastError();
 }
 
 }  // namespace lbm

@@ -48,7 +48,7 @@ def main():
                 fg = L.get_f()
             err = float((np.abs(fg[:, m] - fo[:, m]) / W[:, None]).max()) if m.any() else 0.0
             assert err <= bar, (n, dtype, err)
-    # full size: every CTA walks many work groups (FP32 with its fill stage)
+    # full size: every CTA walks many work groups
     pack = I.sphere_pack(256, 8.0, 0.35, I.SEED_POROUS_256)
     for dtype in ("f64", "f32", "f16s"):
         with lbm.Lattice(pack, dtype, 0b111) as L:
@@ -59,7 +59,7 @@ def main():
             L.step_kernel(lbm.KERNEL_RW, 2)
             mass, _ = L.reduce()
             assert np.isfinite(mass)
-    # the host side: a planted record (code 3: neighbour rank, value 77) fails the next
+    # the host side: a planted record (code 3: gather source, value 77) fails the next
     # step with LBM_EINTERNAL, and the context stays failed
     nt = I.random_box(8, 8, 8, p_solid=0.2, seed=7)
     with lbm.Lattice(nt, "f64", 0b111) as L:
@@ -71,7 +71,7 @@ def main():
             L.step(1)
             raise AssertionError("a planted check record did not fail the step")
         except lbm.LBMError as e:
-            assert e.status == 8 and "neighbour rank" in str(e) and "value 77" in str(e), str(e)
+            assert e.status == 8 and "gather source" in str(e) and "value 77" in str(e), str(e)
         try:
             L.reduce()
             raise AssertionError("the context did not stay failed")

@@ -138,8 +138,8 @@ def _periodic_boxes(dims, seed, n=12):
 # ------------------------------------------------ porous pack, every storage format
 @pytest.mark.parametrize("dtype", ["f64n", "f32", "f16s", "f16sr"])
 def test_porous_256_every_format(pack, dtype):
-    """FP64 all-FP64 arithmetic, FP32 (with its fill stage: LBGK on a geometry with
-    mixed sectors), FP16 round-to-nearest and stochastic rounding, LBGK + Guo."""
+    """FP64 all-FP64 arithmetic, FP32, FP16 round-to-nearest and stochastic rounding,
+    LBGK + Guo."""
     tau, g = 0.7, (1e-5, 2e-6, -1e-6)
     with lbm.Lattice(pack, dtype, 0b111) as L:
         L.set_params(tau, g)
@@ -183,7 +183,7 @@ def test_porous_256_collision_models(pack, eq, coll, dtype):
 # ------------------------------------------------------ dense cavity with moving lid
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_cavity_256_moving_lid(dtype):
-    """Dense 256^3 closed box (no dropped tiles, no fill slots), the face z = nz moving
+    """Dense 256^3 closed box (no dropped tiles, every group full), the face z = nz moving
     along x and y: boxes in the bulk and boxes whose top face is the lid."""
     nt = np.ones((N, N, N), np.uint8)
     tau, u_lid = 0.6, (0.08, 0.03, 0.0)

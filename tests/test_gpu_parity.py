@@ -230,39 +230,65 @@ def test_state_roundtrip_and_mismatch():
         assert e.value.status == 5
 
 
-@pytest.mark.parametrize("dtype", ["f32", "f64", "f16s"])
-def test_solid_slots_keep_their_nan(dtype):
-    """The step stores only into non-solid slots and, for FP32 storage, stores NaN again into
-    the solid and padding slots of every 32-byte sector it writes (full-sector writes): after
-    any number of steps, single launches or graph replays, the raw copy holds the canonical
-    NaN in every solid or padding slot of a kept tile and finite values everywhere else."""
-    nt = I.random_box(13, 10, 9, p_solid=0.45, seed=11)          # ragged: padding slots too
+def _padded_lanes(nt, ne, max_tiles):
+    """Padded lane of every (tile, slot) in the grouped layout the library documents: kept
+    tiles in rank order cut greedily into groups of at most max_tiles tiles and 256
+    non-solid nodes, a tile's nodes on consecutive lanes in slot order; -1 for solid and
+    padding slots."""
     nz, ny, nx = nt.shape
     Tx, Ty = (nx + 3) // 4, (ny + 3) // 4
-    elem, nan_bits, uint = {"f32": (np.float32, 0x7fc00000, np.uint32),
-                            "f64": (np.float64, 0x7ff8000000000000, np.uint64),
-                            "f16s": (np.float16, 0x7e00, np.uint16)}[dtype]
+    s = np.arange(64)
+    t = ne.astype(np.int64)[:, None]
+    x = 4 * (t % Tx) + (s & 3)
+    y = 4 * ((t // Tx) % Ty) + ((s >> 2) & 3)
+    z = 4 * (t // (Tx * Ty)) + (s >> 4)
+    inside = (x < nx) & (y < ny) & (z < nz)
+    nonsolid = np.zeros_like(inside)
+    nonsolid[inside] = nt[z[inside], y[inside], x[inside]] != 0
+    lanes = -np.ones(nonsolid.shape, np.int64)
+    group, used, tiles = 0, 0, 0
+    for k in range(len(ne)):
+        cnt = int(nonsolid[k].sum())
+        if tiles == max_tiles or used + cnt > 256:
+            group, used, tiles = group + 1, 0, 0
+        lanes[k, nonsolid[k]] = 256 * group + used + np.arange(cnt)
+        used += cnt
+        tiles += 1
+    return lanes, group + 1, (x, y, z)
+
+
+@pytest.mark.parametrize("dtype", ["f32", "f64", "f16s"])
+def test_grouped_layout_and_padding_lanes(dtype):
+    """The raw copy (the payload of a saved state) is laid out as documented: storage group
+    g holds one 256-lane data block per direction, f_i of the node on padded lane P at
+    (P // 256, i, P % 256). Every non-solid node's value there is the one lbm_get_f exports,
+    and after any number of steps, single launches or graph replays, the padding lanes of
+    the groups still hold the zeros they were created with: the step writes only its
+    nodes' lanes."""
+    nt = I.random_box(13, 10, 9, p_solid=0.45, seed=11)          # ragged: padding slots too
+    elem, uint = {"f32": (np.float32, np.uint32), "f64": (np.float64, np.uint64),
+                  "f16s": (np.float16, np.uint16)}[dtype]
     with lbm.Lattice(nt, dtype, 0) as L:                          # ragged axes cannot be periodic
         L.set_params(0.7, g=(1e-5, 0.0, 0.0))
         L.init_equilibrium()
         _, ne = L.tiles()
-        s = np.arange(64)
-        t = ne.astype(np.int64)[:, None]
-        x = 4 * (t % Tx) + (s & 3)
-        y = 4 * ((t // Tx) % Ty) + ((s >> 2) & 3)
-        z = 4 * (t // (Tx * Ty)) + (s >> 4)
-        inside = (x < nx) & (y < ny) & (z < nz)
-        solid = ~inside
-        solid[inside] = nt[z[inside], y[inside], x[inside]] == 0
-        assert solid.any() and (~solid).any()
+        lanes, n_groups, (x, y, z) = _padded_lanes(nt, ne, 16 if dtype == "f64" else 8)
+        assert (lanes >= 0).any() and (lanes < 0).any()
+        assert L.info()["copy_bytes"] == n_groups * 19 * 256 * np.dtype(elem).itemsize
         for steps in (1, 1, 2, 16, 17):
             L.step(steps)
             blob = L.save_state()
-            payload = np.frombuffer(blob[len(blob) - len(ne) * 19 * 64 * np.dtype(elem).itemsize:], dtype=elem)
-            f = payload.reshape(len(ne), 19, 64)
-            bits = f.view(uint).transpose(0, 2, 1)                 # [tile][slot][direction]
-            assert (bits[solid] == nan_bits).all()
-            assert np.isfinite(f.transpose(0, 2, 1)[~solid]).all()
+            size = n_groups * 19 * 256 * np.dtype(elem).itemsize
+            f = np.frombuffer(blob[len(blob) - size:], dtype=elem).reshape(n_groups, 19, 256)
+            flat = f.transpose(0, 2, 1).reshape(n_groups * 256, 19)      # [padded lane][direction]
+            used = np.zeros(n_groups * 256, bool)
+            used[lanes[lanes >= 0]] = True
+            assert (flat[~used].view(uint) == 0).all()
+            assert np.isfinite(flat[used]).all()
+            if dtype == "f64":
+                fd = L.get_f()
+                m = lanes >= 0
+                assert np.array_equal(flat[lanes[m]], fd[:, z[m], y[m], x[m]].T)
 
 
 def test_argument_errors():
