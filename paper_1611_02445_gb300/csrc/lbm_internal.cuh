@@ -171,6 +171,10 @@ struct StepParams {
     int zh_face[2];
     // storage group of work group 0 (a slab's lower ghost plane has groups before it)
     int64_t sg0;
+    // always 0: the step kernel ANDs it with the values a thread has read from its staging
+    // column and adds the result to the next gathers' addresses, which orders them after
+    // the reads (the compiler cannot fold it away)
+    uint32_t zero;
     // extents the checked build (LBM_CHECKED) tests every index against (kept tiles,
     // non-solid nodes of the work groups, padded lanes of a copy), and its error word
     // (NULL in the normal build): the first failed check stores (code << 56) | value

@@ -49,23 +49,26 @@ namespace lbm {
 template <int DT> struct StepCfg {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 4;
+    static constexpr int SLOTS = 2;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
 };
 template <> struct StepCfg<LBM_F32> {
     static constexpr int THREADS = 256;
     static constexpr int CTAS = 3;
+    static constexpr int SLOTS = 2;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_4B;
 };
 template <> struct StepCfg<LBM_F64> {
     static constexpr int THREADS = 256;
-    static constexpr int CTAS = 2;
+    static constexpr int CTAS = 3;
+    static constexpr int SLOTS = 1;
     static constexpr int MAX_TILES = GROUP_MAX_TILES_F64;
 };
 static_assert(StepCfg<LBM_F32>::THREADS == GROUP_MAX_NODES && StepCfg<LBM_F64>::THREADS == GROUP_MAX_NODES_F64,
               "work groups and CTAs must agree");
 constexpr int HDR_SLOTS = 4;
 constexpr int META_SLOTS = 3;
-constexpr int DATA_SLOTS = 2;
+constexpr int REC_SLOTS = 2;
 
 // ---------------------------------------------------------------------------- cp.async
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
@@ -123,14 +126,17 @@ struct StepSmem {
     using G = typename Store<DT>::R;
     int4 hdr[HDR_SLOTS];                                   // {t0, tiles, f0, nodes}
     // neighbour records (index of each neighbour's first node) and the nodes' source ranks:
-    // read only when the group's gathers are issued, one iteration after they land, so two
-    // slots (those of the data ring)
-    int64_t rec[DATA_SLOTS][StepCfg<DT>::MAX_TILES][NBR_STRIDE];
-    uint4 rank[DATA_SLOTS][StepCfg<DT>::THREADS];
+    // read only when the group's gathers are issued, one iteration after they land
+    int64_t rec[REC_SLOTS][StepCfg<DT>::MAX_TILES][NBR_STRIDE];
+    uint4 rank[REC_SLOTS][StepCfg<DT>::THREADS];
     uint32_t word[META_SLOTS][StepCfg<DT>::THREADS];
     // F16S: bit i set when direction i's value is the upper half of its staged word
-    uint32_t odd[DATA_SLOTS][DT == LBM_F16S ? StepCfg<DT>::THREADS : 1];
-    E data[DATA_SLOTS][Q][StepCfg<DT>::THREADS];
+    uint32_t odd[StepCfg<DT>::SLOTS][DT == LBM_F16S ? StepCfg<DT>::THREADS : 1];
+    // staging slots: column t of a slot holds thread t's 19 gathered values, written and
+    // read by that thread alone. With one slot the next group's gathers go into the column
+    // as soon as the thread has read the current values into registers; with two they go
+    // into the other slot.
+    E data[StepCfg<DT>::SLOTS][Q][StepCfg<DT>::THREADS];
     // last, so that a launch without a per-node force field leaves it out of the dynamic
     // shared memory (the space goes to the L1 cache, which serves the 4-byte gathers)
     G gf[META_SLOTS][StepCfg<DT>::THREADS];
@@ -164,10 +170,12 @@ __device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, int rslo
 
 // Issue the 19 gathers of this thread's node (for F16S the aligned 32-bit word that holds
 // the wanted half). sg: the group's storage group; the node's own padded lane is
-// 256 sg + t.
+// 256 sg + t. dep is zero, computed from the values the thread has just read out of its
+// staging column, so that no copy into the column is issued before those reads are done.
 template <int DT, int MODE>
-__device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, int64_t sg,
-                                             const typename Store<DT>::T* __restrict__ A, const StepParams& p) {
+__device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int rslot, int dslot, const int4 h, int64_t sg,
+                                             const typename Store<DT>::T* __restrict__ A, const StepParams& p,
+                                             uint32_t dep) {
     const int t = threadIdx.x;
     const uint32_t w = sm.word[mslot][t];
     if (((w >> WORD_TYPE_SHIFT) & 3u) == LBM_SOLID) return;
@@ -175,7 +183,7 @@ __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int ds
     if (!check_ok(lt < h.y, CHECK_OWN_TILE, (int64_t)h.z + t, p)) return;
     const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
     const int64_t own = sg * (Q * GROUP_LANES) + t;
-    const uint4 rk = sm.rank[dslot][t];
+    const uint4 rk = sm.rank[rslot][t];
     uint32_t odd = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
@@ -187,10 +195,11 @@ __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int ds
         } else {
             const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
             const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
-            src = sm.rec[dslot][lt][nb] + i * GROUP_LANES + rank_of(rk, i);
+            src = sm.rec[rslot][lt][nb] + i * GROUP_LANES + rank_of(rk, i);
             if (!check_ok(src >= 0 && src < p.n_padded * Q, CHECK_NEIGHBOUR, ((int64_t)(h.x + lt) << 8) | (nb << 2), p))
                 continue;
         }
+        src += dep;
         if (DT == LBM_F64) {
             cp_async8(&sm.data[dslot][i][t], A + src);
         } else if (DT == LBM_F32) {
@@ -200,7 +209,7 @@ __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int ds
             cp_async4(&sm.data[dslot][i][t], A + (src & ~(int64_t)1));
         }
     }
-    if (DT == LBM_F16S) sm.odd[dslot][t] = odd;
+    if (DT == LBM_F16S) sm.odd[dslot][DT == LBM_F16S ? t : 0] = odd;
 }
 
 // FP16 store of a node's 19 results h (FP32, unscaled) that keeps the node's mass and
@@ -237,32 +246,44 @@ __device__ __forceinline__ void store_f16_conserving(const float v[Q], __half* _
     put(0, v[0] + m);
 }
 
-template <int DT, bool VAR, int MODE, bool GEN>
+// Read this thread's staged values of group g into registers, let `next` issue the
+// gathers of the thread's node in the next group into the same column, then collide
+// and store. A thread without a node in g still calls next.
+template <int DT, bool VAR, int MODE, bool GEN, typename Next>
 __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, int64_t sg,
                                               typename Store<DT>::T* __restrict__ B, const StepParams& p,
-                                              bool has_gf, uint32_t key) {
+                                              bool has_gf, uint32_t key, Next&& next) {
     using R = typename Store<DT>::R;
     using T = typename Store<DT>::T;
     const int t = threadIdx.x;
     const uint32_t w = sm.word[mslot][t];
     const int type = (int)((w >> WORD_TYPE_SHIFT) & 3u);
-    if (type == LBM_SOLID) return;
+    if (type == LBM_SOLID) {
+        next(0u);
+        return;
+    }
     const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     R v[Q];
-    const uint32_t odd = DT == LBM_F16S ? sm.odd[DT == LBM_F16S ? dslot : 0][DT == LBM_F16S ? t : 0] : 0u;
+    const uint32_t odd = DT == LBM_F16S ? sm.odd[dslot][DT == LBM_F16S ? t : 0] : 0u;
+    uint32_t fold = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
         T e;
         if (DT == LBM_F16S) {
             const uint32_t word = (uint32_t)sm.data[dslot][i][t];
+            fold ^= word;
             const unsigned short hbits = (unsigned short)(word >> (((odd >> i) & 1u) << 4));
             e = *reinterpret_cast<const T*>(&hbits);
         } else {
             const typename Staged<DT>::E raw = sm.data[dslot][i][t];
+            fold ^= (uint32_t)raw;
             e = *reinterpret_cast<const T*>(&raw);
         }
         v[i] = to_arith<DT>(e, i);
     }
+    // one slot: 0 (p.zero is 0, unknown to the compiler), but only once every value above
+    // has arrived in its register
+    next(StepCfg<DT>::SLOTS == 1 ? fold & p.zero : 0u);
     const R Fx = has_gf ? sm.gf[mslot][t] : par<R>(p.g[0], p.g_f[0]);
     const R Fy = par<R>(p.g[1], p.g_f[1]), Fz = par<R>(p.g[2], p.g_f[2]);
     if (MODE == STEP_FULL && ((w >> WORD_LID_BIT) & 1u)) {
@@ -308,8 +329,15 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     }
 }
 
+// Resident CTAs per SM of a step instantiation: the collision models (GEN) of the FP64
+// format need more registers than 3 CTAs leave, and run 2.
+template <int DT, bool GEN>
+constexpr int step_ctas() {
+    return DT == LBM_F64 && GEN ? 2 : StepCfg<DT>::CTAS;
+}
+
 template <int DT, bool VAR, int MODE, bool GEN>
-__global__ void __launch_bounds__(StepCfg<DT>::THREADS, StepCfg<DT>::CTAS)
+__global__ void __launch_bounds__(StepCfg<DT>::THREADS, step_ctas<DT, GEN>())
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int64_t* __restrict__ nrec, const uint32_t* __restrict__ fword,
        const uint4* __restrict__ frank, const void* __restrict__ gfield_c, int64_t n_groups, StepParams p, const uint32_t* __restrict__ seed_in,
@@ -343,27 +371,42 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    issue_gather<DT, MODE>(sm, 0, 0, group_header<DT>(sm.hdr[0], p), p.sg0 + g0, A, p);
+    issue_gather<DT, MODE>(sm, 0, 0, 0, group_header<DT>(sm.hdr[0], p), p.sg0 + g0, A, p, 0u);
     cp_async_commit();
+    constexpr int NS = StepCfg<DT>::SLOTS;
     int it = 0;
     for (int64_t g = g0; g < n_groups; g += G, it++) {
-        // pending: header(g + 2G) [done], meta(g + G), gather(g)
-        cp_async_wait<1>();
-        __syncthreads();   // header(g + 2G), meta(g + G) visible; iteration it - 1 finished
+        if constexpr (NS == 2) {
+            // pending: header(g + 2G) [done], meta(g + G), gather(g)
+            cp_async_wait<1>();
+            __syncthreads();   // header(g + 2G), meta(g + G) visible; iteration it - 1 finished
+        } else {
+            cp_async_wait<0>();
+            __syncthreads();   // header(g + 2G), meta(g + G), gather(g) landed; iteration it - 1 finished
+        }
         issue_hdr(&sm.hdr[(it + 3) & 3], g + 3 * G, n_groups, groups);
         cp_async_commit();
         if (g + 2 * G < n_groups)
             issue_meta<DT>(sm, (it + 2) % META_SLOTS, it & 1, group_header<DT>(sm.hdr[(it + 2) & 3], p), nrec, fword,
                            frank, gfield_c);
         cp_async_commit();
-        if (g + G < n_groups)
-            issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, group_header<DT>(sm.hdr[(it + 1) & 3], p),
-                                   p.sg0 + g + G, A, p);
-        cp_async_commit();
-        // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
-        cp_async_wait<3>();
+        auto gather_next = [&](uint32_t dep) {
+            if (g + G < n_groups)
+                issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, (it + 1) % NS,
+                                       group_header<DT>(sm.hdr[(it + 1) & 3], p), p.sg0 + g + G, A, p, dep);
+            cp_async_commit();
+        };
         const int4 h = group_header<DT>(sm.hdr[it & 3], p);
-        compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it & 1, h, p.sg0 + g, B, p, has_gf, key);
+        if constexpr (NS == 2) {
+            // the next group's gathers go into the other slot before this group's are awaited
+            gather_next(0u);
+            cp_async_wait<3>();   // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
+            compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it % NS, h, p.sg0 + g, B, p, has_gf, key,
+                                              [](uint32_t) {});
+        } else {
+            // one slot: each thread refills its column once it has read it
+            compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, 0, h, p.sg0 + g, B, p, has_gf, key, gather_next);
+        }
     }
     cp_async_wait<0>();
 }
@@ -375,7 +418,7 @@ static size_t step_smem(bool with_gf) {
     return with_gf ? sizeof(StepSmem<DT>) : offsetof(StepSmem<DT>, gf);
 }
 
-// Persistent grid of StepCfg::CTAS CTAs per SM. Shared memory and L1 share one array per
+// Persistent grid of step_ctas CTAs per SM. Shared memory and L1 share one array per
 // SM; the kernel's preferred carveout is set to what those CTAs need (with the force
 // staging, the larger case) so that the rest stays L1, which serves the 4-byte gathers
 // (cp.async.ca). Left to itself the driver picks the carveout for the highest occupancy:
@@ -394,13 +437,13 @@ static int step_grid(int64_t n_groups, bool with_gf) {
         cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
         if (smem_sm > 0) {
-            const double need = (double)StepCfg<DT>::CTAS * (double)(sizeof(StepSmem<DT>) + (size_t)reserved);
+            const double need = (double)step_ctas<DT, GEN>() * (double)(sizeof(StepSmem<DT>) + (size_t)reserved);
             const int pct = std::min(100, std::max(1, (int)std::ceil(100.0 * need / smem_sm)));
             cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
         }
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN>, StepCfg<DT>::THREADS,
                                                       step_smem<DT>(with_gf));
-        ps = std::max(1, std::min(ps, StepCfg<DT>::CTAS));
+        ps = std::max(1, std::min(ps, step_ctas<DT, GEN>()));
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)ps * n_sm));
 }
