@@ -100,7 +100,7 @@ LBM_DF_HD DFConst make_df_const(double omega, double beta, double Fx, double Fy,
 // Directions whose fixed-point conversion runs on the FP64 pipe (fix_from_double_cvt);
 // the others use the integer-only fix_from_double. The split balances the FP64 pipe
 // against instruction issue.
-constexpr uint32_t FIX_CVT_DIRS = 0x7fu;
+constexpr uint32_t FIX_CVT_DIRS = 0x1fffu;
 
 // One direction pair (a with velocity c, b with -c) of weight class k, with
 //   cj = c.j', g9 = 9 beta c.F, g3 = 3 beta w c.F, winv = w / rho:
