@@ -62,6 +62,16 @@ LBM_DF_HD dfl df_g3(int k, dfl G3x, dfl G3y, dfl G3z) {
     return k < 3 ? df_g9(k, G3x, G3y, G3z) : df_scale2(df_g9(k, G3x, G3y, G3z), 0.5f);
 }
 
+// Force arguments of pair k for a force along x alone: pairs 0 (1,3), 3 (7,9), 5 (11,14)
+// and 6 (12,13) have c_x = +1 on their first direction, pair 4 (8,10) has c_x = -1; the
+// others have c_x = 0 and no force terms. 9 beta c.F is +-G9x; 3 beta w c.F is G3x for
+// the axis pair and +-G3x / 2 (`half`) for a diagonal one (w2 = w1 / 2).
+LBM_DF_HD bool df_pair_has_fx(int k) { return k == 0 || (k >= 3 && k <= 6); }
+LBM_DF_HD dfl df_pair_g9x(int k, dfl G9x) { return k == 4 ? df_make(-G9x.h, -G9x.l) : G9x; }
+LBM_DF_HD dfl df_pair_g3x(int k, dfl G3x, dfl half) {
+    return k == 0 ? G3x : k == 4 ? df_make(-half.h, -half.l) : half;
+}
+
 LBM_DF_HD dfl df_split_host(double v) {
     const float h = (float)v;
     return df_make(h, (float)(v - (double)h));
@@ -108,11 +118,14 @@ constexpr uint32_t FIX_CVT_DIRS = 0x1fffu;
 // The even part dominates: |omega w rho| >= |w T / rho| and |Ye| >= |Yo| hold while
 // |c.u| < 1/3 (T <= 9 omega j^2, Yo ~ 3 omega w rho c.u), far inside the low-Mach range
 // of the method, so those three sums use FastTwoSum.
-LBM_DF_HD void df_pair(double& a, double& b, const DFConst& K, int k, dfl cj, dfl g9, dfl g3, dfl winv, dfl A,
-                       dfl P) {
-    const dfl T = df_sub(df_mul(cj, df_add(df_mul(K.om45, cj), g9)), P);
+// has_f false: the pair's force terms g9, g3 are zero (c.F = 0) and their sums are left out.
+LBM_DF_HD void df_pair(double& a, double& b, const DFConst& K, int k, dfl cj, bool has_f, dfl g9, dfl g3, dfl winv,
+                       dfl A, dfl P) {
+    const dfl q = df_mul(K.om45, cj);
+    const dfl T = df_sub(df_mul(cj, has_f ? df_add(q, g9) : q), P);
     const dfl Ye = df_add_dom(A, df_mul(winv, T));
-    const dfl Yo = df_add(df_mul(K.ow3[k], cj), g3);
+    const dfl o = df_mul(K.ow3[k], cj);
+    const dfl Yo = has_f ? df_add(o, g3) : o;
     const double yp = df_to_double_pos(df_add_dom(Ye, Yo));
     const double ym = df_to_double_pos(df_sub_dom(Ye, Yo));
 #if defined(__CUDA_ARCH__)
@@ -127,6 +140,10 @@ LBM_DF_HD void df_pair(double& a, double& b, const DFConst& K, int k, dfl cj, df
 // f: the 19 gathered populations of a fluid node, replaced by the post-collision ones.
 // uniform_fx: Fx is the uniform force K was built with, so every term that depends on it
 // comes from K; otherwise (a per-node force field) they are formed here.
+// XF: K was built with F_y = F_z = 0 (a force along x, or none), so the terms of F_y and
+// F_z, and the force terms of the pairs with c_x = 0, are left out; with those inputs the
+// results equal the general form's bit for bit (the omitted sums add exact zeros).
+template <bool XF>
 LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool uniform_fx) {
     // exact moments in 64-bit fixed point, from pair sums s and differences d of
     // opposite directions (the FP64 pipe is kept for the final update)
@@ -143,13 +160,13 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool unifor
     const int64_t jz = d56 + d1114 - d1213 + d1518 - d1617;
     // j' = j + F/2 (F/2 in the same fixed point, truncated: |error| < 2^-58)
     const dfl Jx = df_from_fix(jx + (uniform_fx ? K.Fx2q : fix_from_double(Fx) >> 1));
-    const dfl Jy = df_from_fix(jy + K.Fy2q);
-    const dfl Jz = df_from_fix(jz + K.Fz2q);
+    const dfl Jy = df_from_fix(XF ? jy : jy + K.Fy2q);
+    const dfl Jz = df_from_fix(XF ? jz : jz + K.Fz2q);
     const dfl inv = df_recip(df_from_fix(rho));
     const dfl Fxd = uniform_fx ? K.Fx : df_from_double(Fx);
     // P = 1.5 omega |j'|^2 + 3 beta j'.F: the isotropic second-order part of every Y_i
     const dfl JJ = df_add(df_add(df_mul(Jx, Jx), df_mul(Jy, Jy)), df_mul(Jz, Jz));
-    const dfl JF = df_add(df_add(df_mul(Jx, Fxd), df_mul(Jy, K.Fy)), df_mul(Jz, K.Fz));
+    const dfl JF = XF ? df_mul(Jx, Fxd) : df_add(df_add(df_mul(Jx, Fxd), df_mul(Jy, K.Fy)), df_mul(Jz, K.Fz));
     const dfl P = df_add(df_mul(K.om15, JJ), df_mul(K.b3, JF));
     const dfl winv1 = df_mul(K.w1, inv);
     const dfl winv2 = df_scale2(winv1, 0.5f);
@@ -177,8 +194,11 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool unifor
     // those stay live through the pairs); the x terms come from K with a uniform force.
     const dfl G9x = uniform_fx ? K.G9x : df_mul(K.b9, Fxd);
     const dfl G3x = uniform_fx ? K.G3x : df_mul(K.bw3, Fxd);
-#define LBM_DF_PAIR(a, b, cls, k, cj, winv) \
-    df_pair(f[a], f[b], K, cls, cj, df_g9(k, G9x, K.G9y, K.G9z), df_g3(k, G3x, K.G3y, K.G3z), winv, A[cls], P)
+    // with XF only the pairs with c_x != 0 carry a force
+#define LBM_DF_PAIR(a, b, cls, k, cj, winv)                                                                   \
+    df_pair(f[a], f[b], K, cls, cj, !XF || df_pair_has_fx(k),                                                 \
+            XF ? df_pair_g9x(k, G9x) : df_g9(k, G9x, K.G9y, K.G9z),                                          \
+            XF ? df_pair_g3x(k, G3x, df_scale2(G3x, 0.5f)) : df_g3(k, G3x, K.G3y, K.G3z), winv, A[cls], P)
     LBM_DF_PAIR(1, 3, 1, 0, Jx, winv1);
     LBM_DF_PAIR(2, 4, 1, 1, Jy, winv1);
     LBM_DF_PAIR(5, 6, 1, 2, Jz, winv1);

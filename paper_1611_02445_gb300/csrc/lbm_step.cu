@@ -249,7 +249,7 @@ __device__ __forceinline__ void store_f16_conserving(const float v[Q], __half* _
 // Read this thread's staged values of group g into registers, let `next` issue the
 // gathers of the thread's node in the next group into the same column, then collide
 // and store. A thread without a node in g still calls next.
-template <int DT, bool VAR, int MODE, bool GEN, typename Next>
+template <int DT, bool VAR, int MODE, bool GEN, bool XF, typename Next>
 __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int dslot, const int4 h, int64_t sg,
                                               typename Store<DT>::T* __restrict__ B, const StepParams& p,
                                               bool has_gf, uint32_t key, Next&& next) {
@@ -305,7 +305,7 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
             zou_he<double, false>(v, ct, p);
             ct = LBM_FLUID;
         }
-        if (ct == LBM_FLUID) collide_df(v, (double)Fx, p.dfc, !has_gf);
+        if (ct == LBM_FLUID) collide_df<XF>(v, (double)Fx, p.dfc, !has_gf);
         else collide<R, false>(v, type, p, Fx, Fy, Fz);
     } else {
         collide<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
@@ -336,7 +336,8 @@ constexpr int step_ctas() {
     return DT == LBM_F64 && GEN ? 2 : StepCfg<DT>::CTAS;
 }
 
-template <int DT, bool VAR, int MODE, bool GEN>
+// XF: the FP64 hybrid collision's form for a force along x (F_y = F_z = 0; collide_df).
+template <int DT, bool VAR, int MODE, bool GEN, bool XF>
 __global__ void __launch_bounds__(StepCfg<DT>::THREADS, step_ctas<DT, GEN>())
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int64_t* __restrict__ nrec, const uint32_t* __restrict__ fword,
@@ -401,11 +402,11 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
             // the next group's gathers go into the other slot before this group's are awaited
             gather_next(0u);
             cp_async_wait<3>();   // pending: gather(g), header(g + 3G), meta(g + 2G), gather(g + G)
-            compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, it % NS, h, p.sg0 + g, B, p, has_gf, key,
+            compute_store<DT, VAR, MODE, GEN, XF>(sm, it % META_SLOTS, it % NS, h, p.sg0 + g, B, p, has_gf, key,
                                               [](uint32_t) {});
         } else {
             // one slot: each thread refills its column once it has read it
-            compute_store<DT, VAR, MODE, GEN>(sm, it % META_SLOTS, 0, h, p.sg0 + g, B, p, has_gf, key, gather_next);
+            compute_store<DT, VAR, MODE, GEN, XF>(sm, it % META_SLOTS, 0, h, p.sg0 + g, B, p, has_gf, key, gather_next);
         }
     }
     cp_async_wait<0>();
@@ -424,7 +425,7 @@ static size_t step_smem(bool with_gf) {
 // (cp.async.ca). Left to itself the driver picks the carveout for the highest occupancy:
 // a light kernel (the calibration kinds) would fit a fifth CTA and keep 28 KB of L1
 // instead of 60 KB, and run 25 % slower.
-template <int DT, bool VAR, int MODE, bool GEN>
+template <int DT, bool VAR, int MODE, bool GEN, bool XF>
 static int step_grid(int64_t n_groups, bool with_gf) {
     static int per_sm[2] = {-1, -1}, n_sm = 0;
     int& ps = per_sm[with_gf ? 1 : 0];
@@ -434,38 +435,55 @@ static int step_grid(int64_t n_groups, bool with_gf) {
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, XF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
         if (smem_sm > 0) {
             const double need = (double)step_ctas<DT, GEN>() * (double)(sizeof(StepSmem<DT>) + (size_t)reserved);
             const int pct = std::min(100, std::max(1, (int)std::ceil(100.0 * need / smem_sm)));
-            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, XF>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
         }
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN>, StepCfg<DT>::THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN, XF>, StepCfg<DT>::THREADS,
                                                       step_smem<DT>(with_gf));
         ps = std::max(1, std::min(ps, step_ctas<DT, GEN>()));
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)ps * n_sm));
 }
 
-template <int DT, bool VAR, int MODE, bool GEN>
-static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
+template <int DT, bool VAR, int MODE, bool GEN, bool XF>
+static cudaError_t launch_step_xf(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
     const bool with_gf = c->gfield != nullptr;
-    const int grid = step_grid<DT, VAR, MODE, GEN>(c->n_groups, with_gf);
+    const int grid = step_grid<DT, VAR, MODE, GEN, XF>(c->n_groups, with_gf);
     // the copy read decides which counter is read and which is advanced
     const int from = A == c->f[0] ? 0 : 1;
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
-    k_step<DT, VAR, MODE, GEN><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
+    k_step<DT, VAR, MODE, GEN, XF><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
         (const T*)A, (T*)B, c->groups, c->nrec, c->fword, c->frank, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
         seed_in, seed_out);
     return cudaGetLastError();
 }
 
+// The instantiations with the hybrid FP64 collision (FP64 storage, hybrid arithmetic,
+// LBGK, fused step) have a form for a force along x, taken when F_y = F_z = 0.
+template <int DT, bool VAR, int MODE, bool GEN>
+constexpr bool has_xf_form() {
+    return DT == LBM_F64 && !VAR && MODE == STEP_FULL && !GEN;
+}
+static bool force_along_x(const lbm_ctx* c) { return c->p.g[1] == 0.0 && c->p.g[2] == 0.0; }
+
+template <int DT, bool VAR, int MODE, bool GEN>
+static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
+    if constexpr (has_xf_form<DT, VAR, MODE, GEN>()) {
+        if (force_along_x(c)) return launch_step_xf<DT, VAR, MODE, GEN, true>(c, A, B);
+    }
+    return launch_step_xf<DT, VAR, MODE, GEN, false>(c, A, B);
+}
+
 template <int DT, bool VAR, bool GEN>
 static void prepare_dt(lbm_ctx* c) {
-    step_grid<DT, VAR, STEP_FULL, GEN>(1, c->gfield != nullptr);
+    if constexpr (has_xf_form<DT, VAR, STEP_FULL, GEN>()) step_grid<DT, VAR, STEP_FULL, GEN, true>(1, c->gfield != nullptr);
+    step_grid<DT, VAR, STEP_FULL, GEN, false>(1, c->gfield != nullptr);
 }
 
 template <int MODE, bool GEN>

@@ -4,6 +4,7 @@
 // wrapper (test_df_host.py) holds the bounds.
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 #include <random>
 
 #include "../paper_1611_02445_gb300/csrc/lbm_collide_df.cuh"
@@ -115,7 +116,7 @@ int main() {
         for (int way = 0; way < 2; way++) {
             double g[19];
             for (int i = 0; i < 19; i++) g[i] = f[i];
-            collide_df(g, F[0], K, way == 0);
+            collide_df<false>(g, F[0], K, way == 0);
             LD mass_out = 0;
             for (int i = 0; i < 19; i++) {
                 coll_abs = std::fmax(coll_abs, (double)(fabsl((LD)g[i] - ref[i]) / weight(i)));
@@ -126,5 +127,29 @@ int main() {
     }
     std::printf("collide_abs_over_w %.3e\n", coll_abs);
     std::printf("collide_mass_rel %.3e\n", mass_rel);
+
+    // the form for a force along x (F_y = F_z = 0) against the general form, bit for bit,
+    // with a uniform and a per-node F_x, F_x = 0 included
+    long xf_mismatch = 0;
+    for (int n = 0; n < 100000; n++) {
+        const double tau = 0.51 + 1.5 * U(rng), omega = 1.0 / tau, beta = 1.0 - 0.5 / tau;
+        const double Fx = n % 10 == 0 ? 0.0 : 1e-4 * (2 * U(rng) - 1);
+        const DFConst K = make_df_const(omega, beta, Fx, 0.0, 0.0);
+        double f[19];
+        const double u0[3] = {0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1)};
+        for (int i = 0; i < 19; i++) {
+            const double cu = CV[i][0] * u0[0] + CV[i][1] * u0[1] + CV[i][2] * u0[2];
+            f[i] = (double)weight(i) * (1 + 3 * cu) * (1.0 + 0.02 * (2 * U(rng) - 1));
+        }
+        for (int way = 0; way < 2; way++) {
+            double a[19], b[19];
+            for (int i = 0; i < 19; i++) a[i] = b[i] = f[i];
+            collide_df<false>(a, Fx, K, way == 0);
+            collide_df<true>(b, Fx, K, way == 0);
+            for (int i = 0; i < 19; i++)
+                if (std::memcmp(&a[i], &b[i], sizeof(double)) != 0) xf_mismatch++;
+        }
+    }
+    std::printf("collide_xf_mismatches %ld\n", xf_mismatch);
     return 0;
 }

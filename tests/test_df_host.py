@@ -7,7 +7,9 @@ kernel compiles (lbm_df.cuh, lbm_collide_df.cuh), against long-double references
 - the fixed-point and FP64 to double-float conversions (relative error below 2^-47);
 - the double-float to double conversion (the nearest double, every case);
 - the LBGK + Guo collision of Eq. 2, 3, 7 (agreement with long double per population,
-  and mass, over random states with |u| up to 0.17, 2 % non-equilibrium, tau 0.51..2).
+  and mass, over random states with |u| up to 0.17, 2 % non-equilibrium, tau 0.51..2);
+- its form for a force along x (the terms of F_y, F_z left out) against the general form,
+  bit for bit.
 """
 import os
 import shutil
@@ -51,3 +53,7 @@ def test_hybrid_collision_matches_long_double(measured):
     # about 2^-48 relative per double-float operation: 3.6e-14 of w_i measured
     assert measured["collide_abs_over_w"] <= 1e-13
     assert measured["collide_mass_rel"] <= 5e-14
+
+
+def test_force_along_x_form_equals_the_general_form(measured):
+    assert measured["collide_xf_mismatches"] == 0

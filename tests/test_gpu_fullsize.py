@@ -136,10 +136,12 @@ def _periodic_boxes(dims, seed, n=12):
 
 
 # ------------------------------------------------ porous pack, every storage format
-@pytest.mark.parametrize("dtype", ["f64n", "f32", "f16s", "f16sr"])
+@pytest.mark.parametrize("dtype", ["f64", "f64n", "f32", "f16s", "f16sr"])
 def test_porous_256_every_format(pack, dtype):
-    """FP64 all-FP64 arithmetic, FP32, FP16 round-to-nearest and stochastic rounding,
-    LBGK + Guo."""
+    """FP64 hybrid and all-FP64 arithmetic, FP32, FP16 round-to-nearest and stochastic
+    rounding, LBGK + Guo with a force that has y and z components (for FP64 storage the
+    general form of the hybrid collision; test_gpu_parity's full-size FP64 test runs the
+    form for a force along x)."""
     tau, g = 0.7, (1e-5, 2e-6, -1e-6)
     with lbm.Lattice(pack, dtype, 0b111) as L:
         L.set_params(tau, g)

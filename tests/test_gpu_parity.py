@@ -98,14 +98,16 @@ FP64_MODES = ["f64", "f64n"]
 
 @pytest.mark.parametrize("dtype", FP64_MODES)
 @pytest.mark.parametrize("periodic", [0b000, 0b111, 0b101, 0b010])
-def test_f64_step_random_box(periodic, dtype):
+@pytest.mark.parametrize("g", [(1e-5, 2e-6, -3e-6), (1e-5, 0.0, 0.0)])
+def test_f64_step_random_box(periodic, dtype, g):
+    """A per-node x force with a uniform y, z force, or none (the hybrid FP64 collision's
+    form for a force along x)."""
     rng = np.random.default_rng(periodic)
     nt = I.random_box(12, 8, 16, p_solid=0.3, seed=periodic + 50, boundary=True)
     nt[:4, :4, :4] = I.SOLID
     f0 = I.random_populations(nt, 0.05, seed=periodic)
     gf = 1e-5 * (1 + 0.1 * rng.standard_normal(nt.shape))
-    fg, fo, red, _ = run_pair(nt, f0, 100, periodic, 0.7, (1e-5, 2e-6, -3e-6), gf, (0.05, 0.01, 0.0), 1.0,
-                              dtype=dtype)
+    fg, fo, red, _ = run_pair(nt, f0, 100, periodic, 0.7, g, gf, (0.05, 0.01, 0.0), 1.0, dtype=dtype)
     assert rel_err(fg, fo, nt) <= F64_TOL
     # solid nodes stay NaN in the export
     assert np.isnan(fg[:, nt == 0]).all()
