@@ -707,10 +707,10 @@ FP64_FLOPS_PER_NODE = 331
 # ncu capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean of
 # two launches after three warm-up steps), with the hash (step_source_hash) of the library
 # sources they were captured with; the bench reports them only while the sources match.
-TRAFFIC_PER_LAUNCH_256 = {"sources": "13eae719ccb392c6",
-                          "f64": 1169045248 + 853665152,
-                          "f32": 691253376 + 417177472,
-                          "f16s": 516936192 + 203758336}
+TRAFFIC_PER_LAUNCH_256 = {"sources": "08d6a514471796e2",
+                          "f64": 1174549248 + 853654400,
+                          "f32": 691536384 + 417656320,
+                          "f16s": 517274112 + 204060416}
 
 if __name__ == "__main__":
     main()
