@@ -160,16 +160,17 @@ LBM_DF_HD dfl df_from_double(double d) {
 // Nearest double to hi + lo for a positive value in [2^-40, 2) (the pair need not be
 // normalised, but |lo| must stay below hi/2^20): normalise with FastTwoSum, widen hi
 // exactly, count lo in units of the double's last place and add the count to hi's bit
-// pattern. When hi is a power of two and lo is negative the result lies in the binade
-// below, where the last place is half as large.
+// pattern. When lo is negative the count is taken in the last place of the float just
+// below hi, which differs from hi's own only when hi is a power of two and the result
+// lies in the binade below, where the last place is half as large.
 LBM_DF_HD double df_to_double_pos(dfl x) {
     const float s = LBM_FADD(x.h, x.l);
     const float l = LBM_FSUB(x.l, LBM_FSUB(s, x.h));
     const uint32_t hb = fbits_of(s);
     const uint64_t hi64 = ((uint64_t)((hb >> 3) + (896u << 20)) << 32) | (uint64_t)(hb << 29);
-    // ulp of the double = 2^(E_f - 127 - 52); scale lo by its inverse 2^(179 - E_f)
-    uint32_t sb = (306u << 23) - (hb & 0x7f800000u);
-    if ((hb & 0x007fffffu) == 0u && l < 0.0f) sb += (1u << 23);
+    // ulp of the double = 2^(E_f - 127 - 52); scale lo by its inverse 2^(179 - E_f), with
+    // E_f the exponent of s, or of the float below s when lo is negative
+    const uint32_t sb = (306u << 23) - ((hb - (fbits_of(l) >> 31)) & 0x7f800000u);
     const float q = LBM_FMUL(l, float_of(sb));
 #if defined(__CUDA_ARCH__)
     const int k = __float2int_rn(q);
@@ -202,11 +203,33 @@ LBM_DF_HD int64_t fix_from_double(double d) {
     return (b >> 63) ? -r : r;
 }
 
+// d * 2^58 for 2^-6 <= d < 16, where it is an integer: the 53-bit significand shifted
+// left by E - 1017 (0 to 9), with E the biased exponent. Six integer instructions, no FP64
+// pipe. Any other input (negative, below 2^-6, 16 or more, zero, not finite) sets `bad`
+// and returns an unspecified value; the caller then converts another way. Where this one
+// is valid the value is exact, so fix_from_double and fix_from_double_cvt give the same.
+LBM_DF_HD int64_t fix_from_double_fast(double d, bool& bad) {
+    const uint64_t b = bits_of(d);
+    const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+    const uint32_t s = (hi >> 20) - 1017u;   // the sign bit makes s large for negative d
+    bad |= s > 9u;
+    const uint32_t mh = (hi & 0x000fffffu) | 0x00100000u;
+#if defined(__CUDA_ARCH__)
+    const uint32_t rh = __funnelshift_l(lo, mh, s);
+    const uint32_t rl = lo << (s & 31u);
+#else
+    const uint32_t rh = (uint32_t)(((((uint64_t)mh << 32) | lo) << (s & 15u)) >> 32);
+    const uint32_t rl = lo << (s & 15u);
+#endif
+    return (int64_t)(((uint64_t)rh << 32) | rl);
+}
+
 // d * 2^58 rounded to the nearest integer, ties to even, for normal |d| < 32 (zero and
 // subnormals give 0): the scaling adds 58 to the exponent field with one integer add,
-// and one conversion on the FP64 pipe rounds. It trades the ~25 integer instructions
-// of fix_from_double for one FP64-pipe operation, which GB300 issues at 2 lanes per SM
-// and clock; the sums stay exact, only ties round the other way.
+// and one conversion on the FP64 pipe rounds. Two instructions and one FP64-pipe
+// operation, which GB300 issues at 2 lanes per SM and clock; the step's fallback for
+// populations outside the range of fix_from_double_fast. Sums of these stay exact, only
+// ties round the other way than in fix_from_double.
 LBM_DF_HD int64_t fix_from_double_cvt(double d) {
     const double x = double_of(bits_of(d) + ((uint64_t)FIX_SHIFT << 52));
 #if defined(__CUDA_ARCH__)

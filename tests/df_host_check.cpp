@@ -43,6 +43,29 @@ int main() {
     if (fix_from_double_cvt(0.0) != 0 || fix_from_double_cvt(-0.0) != 0 || fix_from_double_cvt(1e-310) != 0) cvt_bad++;
     std::printf("fix_cvt_mismatches %ld\n", cvt_bad);
 
+    // fix_from_double_fast: flags exactly the inputs outside [2^-6, 16) (negative, zero,
+    // subnormal, infinite and NaN included) and agrees with fix_from_double on all others
+    long fast_bad = 0, fast_flag = 0;
+    for (int n = 0; n < 2000000; n++) {
+        double d = std::ldexp(1.0 + U(rng), (int)(rng() % 16) - 10) * ((rng() % 8 == 0) ? -1.0 : 1.0);
+        if (n % 1000 == 1) d = 0.0;
+        if (n % 1000 == 2) d = -0.0;
+        if (n % 1000 == 3) d = 1e-310;
+        if (n % 1000 == 4) d = INFINITY;
+        if (n % 1000 == 5) d = NAN;
+        if (n % 1000 == 6) d = 0x1p-6;
+        if (n % 1000 == 7) d = std::nextafter(0x1p-6, 0.0);
+        if (n % 1000 == 8) d = std::nextafter(16.0, 0.0);
+        if (n % 1000 == 9) d = 16.0;
+        bool bad = false;
+        const int64_t v = fix_from_double_fast(d, bad);
+        const bool inside = d >= 0x1p-6 && d < 16.0;
+        if (bad == inside) fast_flag++;
+        if (!bad && v != fix_from_double(d)) fast_bad++;
+    }
+    std::printf("fix_fast_mismatches %ld\n", fast_bad);
+    std::printf("fix_fast_flag_errors %ld\n", fast_flag);
+
     // df_from_fix: relative error of hi + lo against x 2^-58
     double fix_rel = 0;
     for (int n = 0; n < 2000000; n++) {
@@ -78,6 +101,7 @@ int main() {
 
     // collide_df against the LBGK + Guo update evaluated in long double
     double coll_abs = 0, mass_rel = 0;
+    long fallback_states = 0;   // states with a population outside [2^-6, 16): the FP64-pipe moments
     for (int n = 0; n < 200000; n++) {
         const double tau = 0.51 + 1.5 * U(rng), omega = 1.0 / tau, beta = 1.0 - 0.5 / tau;
         const double F[3] = {1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1)};
@@ -91,6 +115,9 @@ int main() {
             const double fe = (double)weight(i) * rho0 * (1 + 3 * cu + 4.5 * cu * cu - 1.5 * uu);
             f[i] = fe * (1.0 + 0.02 * (2 * U(rng) - 1));
         }
+        bool outside = false;
+        for (int i = 0; i < 19; i++) outside |= !(f[i] >= 0x1p-6 && f[i] < 16.0);
+        fallback_states += outside;
         LD rho = 0, j[3] = {0, 0, 0};
         for (int i = 0; i < 19; i++) {
             rho += f[i];
@@ -127,6 +154,7 @@ int main() {
     }
     std::printf("collide_abs_over_w %.3e\n", coll_abs);
     std::printf("collide_mass_rel %.3e\n", mass_rel);
+    std::printf("collide_fallback_states %ld\n", fallback_states);
 
     // the form for a force along x (F_y = F_z = 0) against the general form, bit for bit,
     // with a uniform and a per-node F_x, F_x = 0 included

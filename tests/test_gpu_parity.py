@@ -114,6 +114,25 @@ def test_f64_step_random_box(periodic, dtype, g):
 
 
 @pytest.mark.parametrize("dtype", FP64_MODES)
+@pytest.mark.parametrize("g", [(1e-5, 2e-6, -3e-6), (1e-5, 0.0, 0.0)])
+def test_f64_step_populations_outside_fast_conversion_range(dtype, g):
+    """At 40 % of the nodes three diagonal populations are set between -0.05 w and 0.5 w,
+    below 2^-6 and some negative: the hybrid collision then forms the node's moments
+    with its fallback conversion, in the first steps until the collision has relaxed
+    them; the velocity stays small, so the rest of its arithmetic is unchanged."""
+    nt = I.random_box(12, 8, 16, p_solid=0.3, seed=77, boundary=True)
+    f0 = I.random_populations(nt, 0.05, seed=77)
+    rng = np.random.default_rng(77)
+    pick = (rng.random(nt.shape) < 0.4) & (nt != 0)
+    for i in (9, 14, 18):
+        f0[i][pick] = W[i] * rng.uniform(-0.05, 0.5, size=int(pick.sum()))
+    assert (f0[:, nt != 0] < 2.0 ** -6).any() and (f0[:, nt != 0] < 0).any()
+    for steps in (1, 20):
+        fg, fo, _, _ = run_pair(nt, f0, steps, 0b111, 0.7, g, dtype=dtype)
+        assert rel_err(fg, fo, nt) <= F64_TOL
+
+
+@pytest.mark.parametrize("dtype", FP64_MODES)
 @pytest.mark.parametrize("shape", [(13, 9, 11), (5, 6, 7), (4, 4, 4), (21, 3, 9)])
 def test_f64_step_ragged_nonperiodic(shape, dtype):
     nx, ny, nz = shape
