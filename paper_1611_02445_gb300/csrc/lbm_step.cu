@@ -29,6 +29,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstddef>
+#include <type_traits>
 
 #include "lbm_collide.cuh"
 #include "lbm_internal.cuh"
@@ -172,7 +173,11 @@ __device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, int rslo
 // the wanted half). sg: the group's storage group; the node's own padded lane is
 // 256 sg + t. dep is zero, computed from the values the thread has just read out of its
 // staging column, so that no copy into the column is issued before those reads are done.
-template <int DT, int MODE>
+// I32: every element index of a copy is below 2^31 (n_padded * 19 < 2^31, up to 113 M
+// non-solid nodes), so the indices are formed in 32 bits, the neighbour records read as
+// their low words, and each address is one widening multiply-add (2 % faster than the
+// 64-bit arithmetic, which larger contexts take).
+template <int DT, int MODE, bool I32>
 __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int rslot, int dslot, const int4 h, int64_t sg,
                                              const typename Store<DT>::T* __restrict__ A, const StepParams& p,
                                              uint32_t dep) {
@@ -182,12 +187,13 @@ __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int rs
     const int lt = (int)((w >> WORD_LT_SHIFT) & (uint32_t)WORD_LT_MASK), s = (int)((w >> WORD_SLOT_SHIFT) & 63u);
     if (!check_ok(lt < h.y, CHECK_OWN_TILE, (int64_t)h.z + t, p)) return;
     const int x = s & 3, y = (s >> 2) & 3, z = s >> 4;
-    const int64_t own = sg * (Q * GROUP_LANES) + t;
+    using IX = typename std::conditional<I32, int32_t, int64_t>::type;
+    const IX own = (IX)(sg * (Q * GROUP_LANES)) + t;
     const uint4 rk = sm.rank[rslot][t];
     uint32_t odd = 0;
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        int64_t src;
+        IX src;
         if (MODE == STEP_RW || i == 0) {
             src = own + i * GROUP_LANES;   // the rest population, or read/write only: the node's own values
         } else if ((w >> i) & 1) {
@@ -195,18 +201,21 @@ __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int rs
         } else {
             const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
             const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
-            src = sm.rec[rslot][lt][nb] + i * GROUP_LANES + rank_of(rk, i);
+            if constexpr (I32)   // the record's low word (little-endian): the index itself
+                src = reinterpret_cast<const int32_t*>(&sm.rec[rslot][lt][nb])[0] + i * GROUP_LANES + (IX)rank_of(rk, i);
+            else
+                src = sm.rec[rslot][lt][nb] + i * GROUP_LANES + rank_of(rk, i);
             if (!check_ok(src >= 0 && src < p.n_padded * Q, CHECK_NEIGHBOUR, ((int64_t)(h.x + lt) << 8) | (nb << 2), p))
                 continue;
         }
-        src += dep;
+        src += (IX)dep;
         if (DT == LBM_F64) {
             cp_async8(&sm.data[dslot][i][t], A + src);
         } else if (DT == LBM_F32) {
             cp_async4(&sm.data[dslot][i][t], A + src);
         } else {
             odd |= (uint32_t)(src & 1) << i;
-            cp_async4(&sm.data[dslot][i][t], A + (src & ~(int64_t)1));
+            cp_async4(&sm.data[dslot][i][t], A + (src & ~(IX)1));
         }
     }
     if (DT == LBM_F16S) sm.odd[dslot][DT == LBM_F16S ? t : 0] = odd;
@@ -337,7 +346,8 @@ constexpr int step_ctas() {
 }
 
 // XF: the FP64 hybrid collision's form for a force along x (F_y = F_z = 0; collide_df).
-template <int DT, bool VAR, int MODE, bool GEN, bool XF>
+// I32: 32-bit gather indices (issue_gather).
+template <int DT, bool VAR, int MODE, bool GEN, bool XF, bool I32>
 __global__ void __launch_bounds__(StepCfg<DT>::THREADS, step_ctas<DT, GEN>())
 k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __restrict__ B,
        const int4* __restrict__ groups, const int64_t* __restrict__ nrec, const uint32_t* __restrict__ fword,
@@ -372,7 +382,7 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    issue_gather<DT, MODE>(sm, 0, 0, 0, group_header<DT>(sm.hdr[0], p), p.sg0 + g0, A, p, 0u);
+    issue_gather<DT, MODE, I32>(sm, 0, 0, 0, group_header<DT>(sm.hdr[0], p), p.sg0 + g0, A, p, 0u);
     cp_async_commit();
     constexpr int NS = StepCfg<DT>::SLOTS;
     int it = 0;
@@ -393,7 +403,7 @@ k_step(const typename Store<DT>::T* __restrict__ A, typename Store<DT>::T* __res
         cp_async_commit();
         auto gather_next = [&](uint32_t dep) {
             if (g + G < n_groups)
-                issue_gather<DT, MODE>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, (it + 1) % NS,
+                issue_gather<DT, MODE, I32>(sm, (it + 1) % META_SLOTS, (it + 1) & 1, (it + 1) % NS,
                                        group_header<DT>(sm.hdr[(it + 1) & 3], p), p.sg0 + g + G, A, p, dep);
             cp_async_commit();
         };
@@ -425,7 +435,7 @@ static size_t step_smem(bool with_gf) {
 // (cp.async.ca). Left to itself the driver picks the carveout for the highest occupancy:
 // a light kernel (the calibration kinds) would fit a fifth CTA and keep 28 KB of L1
 // instead of 60 KB, and run 25 % slower.
-template <int DT, bool VAR, int MODE, bool GEN, bool XF>
+template <int DT, bool VAR, int MODE, bool GEN, bool XF, bool I32>
 static int step_grid(int64_t n_groups, bool with_gf) {
     static int per_sm[2] = {-1, -1}, n_sm = 0;
     int& ps = per_sm[with_gf ? 1 : 0];
@@ -435,33 +445,42 @@ static int step_grid(int64_t n_groups, bool with_gf) {
         cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
         cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
-        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, XF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, XF, I32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)sizeof(StepSmem<DT>));
         if (smem_sm > 0) {
             const double need = (double)step_ctas<DT, GEN>() * (double)(sizeof(StepSmem<DT>) + (size_t)reserved);
             const int pct = std::min(100, std::max(1, (int)std::ceil(100.0 * need / smem_sm)));
-            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, XF>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+            cudaFuncSetAttribute(k_step<DT, VAR, MODE, GEN, XF, I32>, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
         }
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN, XF>, StepCfg<DT>::THREADS,
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_step<DT, VAR, MODE, GEN, XF, I32>, StepCfg<DT>::THREADS,
                                                       step_smem<DT>(with_gf));
         ps = std::max(1, std::min(ps, step_ctas<DT, GEN>()));
     }
     return (int)std::max<int64_t>(1, std::min<int64_t>(n_groups, (int64_t)ps * n_sm));
 }
 
-template <int DT, bool VAR, int MODE, bool GEN, bool XF>
-static cudaError_t launch_step_xf(lbm_ctx* c, const void* A, void* B) {
+// 32-bit gather indices when every element index of a copy fits (issue_gather).
+static bool idx32(const lbm_ctx* c) { return c->p.n_padded * (int64_t)Q < (int64_t(1) << 31); }
+
+template <int DT, bool VAR, int MODE, bool GEN, bool XF, bool I32>
+static cudaError_t launch_step_ix(lbm_ctx* c, const void* A, void* B) {
     using T = typename Store<DT>::T;
     const bool with_gf = c->gfield != nullptr;
-    const int grid = step_grid<DT, VAR, MODE, GEN, XF>(c->n_groups, with_gf);
+    const int grid = step_grid<DT, VAR, MODE, GEN, XF, I32>(c->n_groups, with_gf);
     // the copy read decides which counter is read and which is advanced
     const int from = A == c->f[0] ? 0 : 1;
     const uint32_t* seed_in = c->seed ? c->seed + from : nullptr;
     uint32_t* seed_out = c->seed ? c->seed + (1 - from) : nullptr;
-    k_step<DT, VAR, MODE, GEN, XF><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
+    k_step<DT, VAR, MODE, GEN, XF, I32><<<grid, StepCfg<DT>::THREADS, step_smem<DT>(with_gf), c->stream>>>(
         (const T*)A, (T*)B, c->groups, c->nrec, c->fword, c->frank, c->gfield ? c->gfield_c : nullptr, c->n_groups, c->p,
         seed_in, seed_out);
     return cudaGetLastError();
+}
+
+template <int DT, bool VAR, int MODE, bool GEN, bool XF>
+static cudaError_t launch_step_xf(lbm_ctx* c, const void* A, void* B) {
+    return idx32(c) ? launch_step_ix<DT, VAR, MODE, GEN, XF, true>(c, A, B)
+                    : launch_step_ix<DT, VAR, MODE, GEN, XF, false>(c, A, B);
 }
 
 // The instantiations with the hybrid FP64 collision (FP64 storage, hybrid arithmetic,
@@ -480,10 +499,17 @@ static cudaError_t launch_step_dt(lbm_ctx* c, const void* A, void* B) {
     return launch_step_xf<DT, VAR, MODE, GEN, false>(c, A, B);
 }
 
+template <int DT, bool VAR, bool GEN, bool I32>
+static void prepare_ix(lbm_ctx* c) {
+    if constexpr (has_xf_form<DT, VAR, STEP_FULL, GEN>())
+        step_grid<DT, VAR, STEP_FULL, GEN, true, I32>(1, c->gfield != nullptr);
+    step_grid<DT, VAR, STEP_FULL, GEN, false, I32>(1, c->gfield != nullptr);
+}
+
 template <int DT, bool VAR, bool GEN>
 static void prepare_dt(lbm_ctx* c) {
-    if constexpr (has_xf_form<DT, VAR, STEP_FULL, GEN>()) step_grid<DT, VAR, STEP_FULL, GEN, true>(1, c->gfield != nullptr);
-    step_grid<DT, VAR, STEP_FULL, GEN, false>(1, c->gfield != nullptr);
+    if (idx32(c)) prepare_ix<DT, VAR, GEN, true>(c);
+    else prepare_ix<DT, VAR, GEN, false>(c);
 }
 
 template <int MODE, bool GEN>
