@@ -719,10 +719,10 @@ FP64_FLOPS_PER_NODE = 331
 # ncu capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean of
 # two launches after three warm-up steps), with the hash (step_source_hash) of the library
 # sources they were captured with; the bench reports them only while the sources match.
-TRAFFIC_PER_LAUNCH_256 = {"sources": "08d6a514471796e2",
-                          "f64": 1174549248 + 853654400,
-                          "f32": 691536384 + 417656320,
-                          "f16s": 517274112 + 204060416}
+TRAFFIC_PER_LAUNCH_256 = {"sources": "04897234c7e29dff",
+                          "f64": 1194566784 + 855974016,
+                          "f32": 687296128 + 416359680,
+                          "f16s": 512587904 + 203284864}
 
 if __name__ == "__main__":
     main()

@@ -207,6 +207,36 @@ def test_cavity_256_moving_lid(dtype):
     print(f"cavity 256^3 lid {dtype}: worst {worst:.3e} of the bar")
 
 
+# ------------------------------------- a context beyond the 32-bit gather indices
+def test_cavity_512_fp64_with_64bit_gather_indices():
+    """Dense 512^3 closed box with the lid, FP64 (41 GB for the two copies): 134 M nodes in
+    full groups, so a copy has 512^3 * 19 > 2^31 elements and the step forms its gather
+    indices in 64 bits (the instantiation every smaller context leaves unused)."""
+    n = 512
+    assert n ** 3 * 19 >= 2 ** 31
+    nt = np.ones((n, n, n), np.uint8)
+    tau, u_lid = 0.6, (0.08, 0.03, 0.0)
+    top = np.zeros((10, 10, 10), bool)
+    top[1:, 1:-1, 1:-1] = True
+    boxes = [b for b in _periodic_boxes((n, n, n), 5) if 0 < b[2] and b[2] + 10 <= n and
+             0 < b[0] and b[0] + 10 <= n and 0 < b[1] and b[1] + 10 <= n]
+    boxes += [(x, y, n - 10, 10, 10, 10, top) for (x, y) in ((5, 7), (n // 2 - 8, 3 * n // 4), (n - 11, 3))]
+    # a box in the last tiles of the copy, where the 64-bit indices are largest
+    boxes += [(n - 11, n - 11, n - 21, 10, 10, 10, _interior())]
+    with lbm.Lattice(nt, "f64", 0) as L:
+        assert L.info()["n_nonsolid"] == n ** 3
+        L.set_params(tau)
+        L.set_lid(5, u_lid)
+        L.init_equilibrium(1.0, U0)
+
+        def ostep(A, b):
+            lid = 5 if b[2] + b[5] == n else -1
+            return O.step_m(A, _crop(nt, *b[:6], wrap=False), 0, tau, lid_face=lid, lid_u=u_lid)
+
+        worst = _sampled(L, boxes, ostep, "f64", steps_before=4)
+    print(f"cavity 512^3 lid f64 (64-bit gather indices): worst {worst:.3e} of the bar")
+
+
 # ----------------------------------------------- Zou-He duct longer than the grid
 @pytest.mark.parametrize("dtype", ["f64", "f32"])
 def test_zou_he_duct_many_groups(dtype):
