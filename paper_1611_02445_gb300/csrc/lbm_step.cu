@@ -84,6 +84,12 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async8_sa(unsigned sa, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async4_sa(unsigned sa, const void* gmem) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
@@ -172,7 +178,11 @@ __device__ __forceinline__ void issue_meta(StepSmem<DT>& sm, int mslot, int rslo
 // Issue the 19 gathers of this thread's node (for F16S the aligned 32-bit word that holds
 // the wanted half). sg: the group's storage group; the node's own padded lane is
 // 256 sg + t. dep is zero, computed from the values the thread has just read out of its
-// staging column, so that no copy into the column is issued before those reads are done.
+// staging column, and added to the column's shared address, so that no copy into the
+// column is issued before those reads are done. A pull of direction i reads entry
+// 13 + dx + 3 dy + 9 dz of the tile's neighbour records, dx = -1 for c_x = +1 at x = 0 and
+// +1 for c_x = -1 at x = 3 (likewise y, z): the six byte offsets of those entries are
+// formed once per node.
 // I32: every element index of a copy is below 2^31 (n_padded * 19 < 2^31, up to 113 M
 // non-solid nodes), so the indices are formed in 32 bits, the neighbour records read as
 // their low words, and each address is one widening multiply-add (2 % faster than the
@@ -191,31 +201,37 @@ __device__ __forceinline__ void issue_gather(StepSmem<DT>& sm, int mslot, int rs
     const IX own = (IX)(sg * (Q * GROUP_LANES)) + t;
     const uint4 rk = sm.rank[rslot][t];
     uint32_t odd = 0;
+    // byte offsets, from the record of the own tile (entry 13), of the neighbour records a
+    // pull along each axis reaches: c = +1 reads the tile at a - 1, c = -1 the one at a + 1
+    const char* r13 = reinterpret_cast<const char*>(&sm.rec[rslot][lt][13]);
+    const int oxm = ((x - 1) >> 2) * 8, oxp = ((x + 1) >> 2) * 8;
+    const int oym = ((y - 1) >> 2) * 24, oyp = ((y + 1) >> 2) * 24;
+    const int ozm = ((z - 1) >> 2) * 72, ozp = ((z + 1) >> 2) * 72;
+    // shared address of this thread's staging column; dep orders the copies after the reads
+    const unsigned sdst = (unsigned)__cvta_generic_to_shared(&sm.data[dslot][0][t]) + dep;
+    constexpr unsigned ROW = StepCfg<DT>::THREADS * sizeof(typename Staged<DT>::E);
 #pragma unroll
     for (int i = 0; i < Q; i++) {
-        IX src;
+        IX rel;   // source index minus 256 i
         if (MODE == STEP_RW || i == 0) {
-            src = own + i * GROUP_LANES;   // the rest population, or read/write only: the node's own values
-        } else if ((w >> i) & 1) {
-            src = own + inv(i) * GROUP_LANES;
+            rel = own;
         } else {
-            const int sx = x - cx(i), sy = y - cy(i), sz = z - cz(i);
-            const int nb = 13 + (sx >> 2) + 3 * (sy >> 2) + 9 * (sz >> 2);
-            if constexpr (I32)   // the record's low word (little-endian): the index itself
-                src = reinterpret_cast<const int32_t*>(&sm.rec[rslot][lt][nb])[0] + i * GROUP_LANES + (IX)rank_of(rk, i);
-            else
-                src = sm.rec[rslot][lt][nb] + i * GROUP_LANES + rank_of(rk, i);
-            if (!check_ok(src >= 0 && src < p.n_padded * Q, CHECK_NEIGHBOUR, ((int64_t)(h.x + lt) << 8) | (nb << 2), p))
+            const int off = (cx(i) > 0 ? oxm : cx(i) < 0 ? oxp : 0) + (cy(i) > 0 ? oym : cy(i) < 0 ? oyp : 0) +
+                            (cz(i) > 0 ? ozm : cz(i) < 0 ? ozp : 0);
+            const IX nrel = *reinterpret_cast<const IX*>(r13 + off) + (IX)rank_of(rk, i);   // I32: the low word
+            rel = ((w >> i) & 1) ? own + (inv(i) - i) * GROUP_LANES : nrel;
+            if (!check_ok(rel + i * GROUP_LANES >= 0 && rel + i * GROUP_LANES < p.n_padded * Q, CHECK_NEIGHBOUR,
+                          ((int64_t)(h.x + lt) << 8) | ((13 + off / 8) << 2), p))
                 continue;
         }
-        src += (IX)dep;
+        const IX src = rel + i * GROUP_LANES;
         if (DT == LBM_F64) {
-            cp_async8(&sm.data[dslot][i][t], A + src);
+            cp_async8_sa(sdst + i * ROW, A + src);
         } else if (DT == LBM_F32) {
-            cp_async4(&sm.data[dslot][i][t], A + src);
+            cp_async4_sa(sdst + i * ROW, A + src);
         } else {
             odd |= (uint32_t)(src & 1) << i;
-            cp_async4(&sm.data[dslot][i][t], A + (src & ~(IX)1));
+            cp_async4_sa(sdst + i * ROW, A + (src & ~(IX)1));
         }
     }
     if (DT == LBM_F16S) sm.odd[dslot][DT == LBM_F16S ? t : 0] = odd;
