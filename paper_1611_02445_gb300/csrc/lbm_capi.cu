@@ -679,6 +679,7 @@ lbm_status lbm_set_params(lbm_ctx* c, double tau, const double* g, const double*
     c->p.gfield = c->gfield;
     drop_graphs(c);   // captured launches hold the old parameters
     c->p.dfc = lbm::make_df_const(c->p.omega, c->p.beta, c->p.g[0], c->p.g[1], c->p.g[2]);
+    c->p.dfb = lbm::make_df_closure(c->p.u_in, c->p.rho_out);
     c->p.omega_f = (float)c->p.omega;
     c->p.beta_f = (float)c->p.beta;
     for (int a = 0; a < 3; a++) {

@@ -100,6 +100,37 @@ LBM_DF_HD DFConst make_df_const(double omega, double beta, double Fx, double Fy,
     return c;
 }
 
+// Per-launch constants of the equilibrium closures of inlet and outlet nodes (the boundary
+// scheme LBM_BC_EQUILIBRIUM): an inlet node takes f^eq(rho, u_in) from its own density,
+// i.e. rho times kin_i = w_i (1 + 3 c.u_in + 4.5 (c.u_in)^2 - 1.5 |u_in|^2), held here with
+// the 2^-58 of the fixed-point density folded in; an outlet node takes f^eq(rho_out, u)
+// with its own velocity, whose weights w rho_out come per class, in pairs.
+struct DFClosure {
+    double kin[19];
+    dfl wout[3], w3out[3];   // w rho_out, 3 w rho_out
+};
+
+LBM_DF_HD DFClosure make_df_closure(const double u_in[3], double rho_out) {
+    // D3Q19 velocities in the library's numbering: 0 rest; 1 E 2 N 3 W 4 S 5 T 6 B;
+    // 7 NE 8 NW 9 SW 10 SE; 11 ET 12 EB 13 WT 14 WB; 15 NT 16 NB 17 ST 18 SB
+    const int c[19][3] = {{0, 0, 0},   {1, 0, 0},  {0, 1, 0},   {-1, 0, 0}, {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                          {1, 1, 0},   {-1, 1, 0}, {-1, -1, 0}, {1, -1, 0}, {1, 0, 1},  {1, 0, -1}, {-1, 0, 1},
+                          {-1, 0, -1}, {0, 1, 1},  {0, 1, -1},  {0, -1, 1}, {0, -1, -1}};
+    const double w[3] = {1.0 / 3.0, 1.0 / 18.0, 1.0 / 36.0};
+    const double uu = u_in[0] * u_in[0] + u_in[1] * u_in[1] + u_in[2] * u_in[2];
+    DFClosure b;
+    for (int i = 0; i < 19; i++) {
+        const double cu = c[i][0] * u_in[0] + c[i][1] * u_in[1] + c[i][2] * u_in[2];
+        const double wi = w[i == 0 ? 0 : i < 7 ? 1 : 2];
+        b.kin[i] = wi * (1.0 + 3.0 * cu + 4.5 * cu * cu - 1.5 * uu) * (1.0 / (double)(1ull << FIX_SHIFT));
+    }
+    for (int k = 0; k < 3; k++) {
+        b.wout[k] = df_split_host(w[k] * rho_out);
+        b.w3out[k] = df_split_host(3.0 * w[k] * rho_out);
+    }
+    return b;
+}
+
 // One direction pair (a with velocity c, b with -c) of weight class k, with cj = c.j',
 // g3 = 3 beta w c.F, AP = omega w rho - (w / rho) P (per weight class), r15 = 1.5 / rho:
 //   Yo = 3 omega w cj + g3,   Ye = AP + r15 cj (Yo + g3).
@@ -136,6 +167,24 @@ LBM_DF_HD void fix_moments(const int64_t q[19], int64_t& rho, int64_t& jx, int64
     jz = d56 + d1114 - d1213 + d1518 - d1617;
 }
 
+// Exact moments of a node in 64-bit fixed point. Populations in [2^-6, 16), every one of a
+// node near equilibrium at |u| below about 0.15, convert with six integer instructions
+// each; a node with any other value (negative, smaller, larger) converts all 19 again on
+// the FP64 pipe, which rounds the small ones to nearest. That fallback needs few
+// registers; the general integer conversion in its place made the whole step 10 % slower.
+LBM_DF_HD void node_moments(const double f[19], int64_t& rho, int64_t& jx, int64_t& jy, int64_t& jz) {
+    int64_t q[19];
+    bool bad = false;
+#pragma unroll
+    for (int i = 0; i < 19; i++) q[i] = fix_from_double_fast(f[i], bad);
+    fix_moments(q, rho, jx, jy, jz);
+    if (bad) {
+#pragma unroll
+        for (int i = 0; i < 19; i++) q[i] = fix_from_double_cvt(f[i]);
+        fix_moments(q, rho, jx, jy, jz);
+    }
+}
+
 // f: the 19 gathered populations of a fluid node, replaced by the post-collision ones.
 // uniform_fx: Fx is the uniform force K was built with, so every term that depends on it
 // comes from K; otherwise (a per-node force field) they are formed here.
@@ -144,24 +193,8 @@ LBM_DF_HD void fix_moments(const int64_t q[19], int64_t& rho, int64_t& jx, int64
 // results equal the general form's bit for bit (the omitted sums add exact zeros).
 template <bool XF>
 LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool uniform_fx) {
-    // Exact moments in 64-bit fixed point. Populations in [2^-6, 16), every one of a node
-    // near equilibrium at |u| below about 0.15, convert with six integer instructions each;
-    // a node with any other value (negative, smaller, larger) converts all 19 again on the
-    // FP64 pipe, which rounds the small ones to nearest. That fallback needs few registers;
-    // the general integer conversion in its place made the whole step 10 % slower.
     int64_t rho, jx, jy, jz;
-    {
-        int64_t q[19];
-        bool bad = false;
-#pragma unroll
-        for (int i = 0; i < 19; i++) q[i] = fix_from_double_fast(f[i], bad);
-        fix_moments(q, rho, jx, jy, jz);
-        if (bad) {
-#pragma unroll
-            for (int i = 0; i < 19; i++) q[i] = fix_from_double_cvt(f[i]);
-            fix_moments(q, rho, jx, jy, jz);
-        }
-    }
+    node_moments(f, rho, jx, jy, jz);
     // j' = j + F/2 (F/2 in the same fixed point, truncated: |error| < 2^-58)
     const dfl Jx = df_from_fix(jx + (uniform_fx ? K.Fx2q : fix_from_double(Fx) >> 1));
     const dfl Jy = df_from_fix(XF ? jy : jy + K.Fy2q);
@@ -209,6 +242,51 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool unifor
     LBM_DF_PAIR(15, 18, 2, 7, df_add(Jy, Jz), AP2);
     LBM_DF_PAIR(16, 17, 2, 8, df_sub(Jy, Jz), AP2);
 #undef LBM_DF_PAIR
+}
+
+// Equilibrium closure of an inlet (type 2) or outlet (type 3) node, replacing the 19
+// gathered populations f: the inlet's f^eq(rho, u_in) is its exact density times the
+// per-launch kin_i, one FP64 multiply per population; the outlet's f^eq(rho_out, u),
+// u = (j + F/2) / rho, is formed in double-float like the collision's pairs,
+//     f_a, f_b = E +- O,  E = w rho_out (1 - 1.5 |u|^2 + 4.5 (c.u)^2),  O = 3 w rho_out c.u,
+// and widened to FP64 without an FP64 instruction. Both keep the closures off the FP64
+// pipe's long dependent chains, which held the rest of a CTA at its per-group barrier.
+LBM_DF_HD void closure_df(double f[19], int type, double Fx, const DFConst& K, const DFClosure& B, bool uniform_fx) {
+    int64_t rho, jx, jy, jz;
+    node_moments(f, rho, jx, jy, jz);
+    if (type == 2) {   // LBM_INLET
+#if defined(__CUDA_ARCH__)
+        const double r = __ll2double_rn(rho);
+#pragma unroll
+        for (int i = 0; i < 19; i++) f[i] = __dmul_rn(r, B.kin[i]);
+#else
+        const double r = (double)rho;
+        for (int i = 0; i < 19; i++) f[i] = r * B.kin[i];
+#endif
+        return;
+    }
+    const dfl inv = df_recip(df_from_fix(rho));
+    const dfl ux = df_mul(df_from_fix(jx + (uniform_fx ? K.Fx2q : fix_from_double(Fx) >> 1)), inv);
+    const dfl uy = df_mul(df_from_fix(jy + K.Fy2q), inv);
+    const dfl uz = df_mul(df_from_fix(jz + K.Fz2q), inv);
+    const dfl uu = df_add(df_add(df_mul(ux, ux), df_mul(uy, uy)), df_mul(uz, uz));
+    const dfl E0 = df_add_dom(df_make(1.0f, 0.0f), df_mulf(uu, -1.5f));   // 1 - 1.5 |u|^2
+    f[0] = df_to_double_pos(df_mul(B.wout[0], E0));
+    auto pair = [&](double& a, double& b, int k, dfl cu) {
+        const dfl E = df_mul(B.wout[k], df_add_dom(E0, df_mulf(df_mul(cu, cu), 4.5f)));
+        const dfl O = df_mul(B.w3out[k], cu);
+        a = df_to_double_pos(df_add_dom(E, O));
+        b = df_to_double_pos(df_sub_dom(E, O));
+    };
+    pair(f[1], f[3], 1, ux);
+    pair(f[2], f[4], 1, uy);
+    pair(f[5], f[6], 1, uz);
+    pair(f[7], f[9], 2, df_add(ux, uy));
+    pair(f[8], f[10], 2, df_sub(uy, ux));
+    pair(f[11], f[14], 2, df_add(ux, uz));
+    pair(f[12], f[13], 2, df_sub(ux, uz));
+    pair(f[15], f[18], 2, df_add(uy, uz));
+    pair(f[16], f[17], 2, df_sub(uy, uz));
 }
 
 }  // namespace lbm

@@ -153,6 +153,7 @@ struct StepParams {
     double rho_out;
     const void* gfield;
     DFConst dfc;   // constants of the double-float FP64 collision
+    DFClosure dfb; // and of its inlet and outlet closures
     // FP32 copies for the 4-byte formats (an FP64 -> FP32 conversion runs on the FP64 pipe)
     float omega_f, beta_f, g_f[3], u_in_f[3], rho_out_f, rho_out_m1_f;
     // collision model (lbm_set_model): equilibrium (LBM_EQ_*) and collision (LBM_COLL_*);
@@ -172,8 +173,8 @@ struct StepParams {
     // storage group of work group 0 (a slab's lower ghost plane has groups before it)
     int64_t sg0;
     // always 0: the step kernel ANDs it with the values a thread has read from its staging
-    // column and adds the result to the next gathers' addresses, which orders them after
-    // the reads (the compiler cannot fold it away)
+    // column and adds the result to the shared address the next gathers copy into, which
+    // orders them after the reads (the compiler cannot fold it away)
     uint32_t zero;
     // extents the checked build (LBM_CHECKED) tests every index against (kept tiles,
     // non-solid nodes of the work groups, padded lanes of a copy), and its error word

@@ -324,14 +324,15 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
         collide_model<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
     } else if constexpr (DT == LBM_F64 && !VAR) {
         // FP64 storage: double-float collision for fluid nodes (and Zou-He boundary nodes
-        // once completed), FP64 for the equilibrium closures
+        // once completed), and the equilibrium closures of inlet and outlet nodes in the
+        // same hybrid arithmetic
         int ct = type;
         if (ct != LBM_FLUID && p.bc == LBM_BC_ZOU_HE) {
             zou_he<double, false>(v, ct, p);
             ct = LBM_FLUID;
         }
         if (ct == LBM_FLUID) collide_df<XF>(v, (double)Fx, p.dfc, !has_gf);
-        else collide<R, false>(v, type, p, Fx, Fy, Fz);
+        else closure_df(v, ct, (double)Fx, p.dfc, p.dfb, !has_gf);
     } else {
         collide<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
     }
@@ -353,6 +354,8 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
         for (int i = 0; i < Q; i++) B[own + i * GROUP_LANES] = to_store<DT>(v[i], i);
     }
 }
+
+static_assert(LBM_INLET == 2 && LBM_OUTLET == 3, "closure_df takes the node types by value");
 
 // Resident CTAs per SM of a step instantiation: the collision models (GEN) of the FP64
 // format need more registers than 3 CTAs leave, and run 2.

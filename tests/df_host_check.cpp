@@ -156,6 +156,46 @@ int main() {
     std::printf("collide_mass_rel %.3e\n", mass_rel);
     std::printf("collide_fallback_states %ld\n", fallback_states);
 
+    // closure_df: inlet f^eq(rho, u_in) and outlet f^eq(rho_out, (j + F/2) / rho) against
+    // long double, with a uniform and a per-node F_x
+    double close_abs = 0;
+    for (int n = 0; n < 100000; n++) {
+        const double tau = 0.51 + 1.5 * U(rng), omega = 1.0 / tau, beta = 1.0 - 0.5 / tau;
+        const double F[3] = {1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1)};
+        const double uin[3] = {0.1 * (2 * U(rng) - 1), 0.05 * (2 * U(rng) - 1), 0.05 * (2 * U(rng) - 1)};
+        const double rho_out = 0.95 + 0.1 * U(rng);
+        const DFConst K = make_df_const(omega, beta, F[0], F[1], F[2]);
+        const DFClosure Bc = make_df_closure(uin, rho_out);
+        double f[19];
+        const double u0[3] = {0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1)};
+        for (int i = 0; i < 19; i++) {
+            const double cu = CV[i][0] * u0[0] + CV[i][1] * u0[1] + CV[i][2] * u0[2];
+            f[i] = (double)weight(i) * (1 + 3 * cu) * (1.0 + 0.02 * (2 * U(rng) - 1));
+        }
+        LD rho = 0, j[3] = {0, 0, 0};
+        for (int i = 0; i < 19; i++) {
+            rho += f[i];
+            for (int a = 0; a < 3; a++) j[a] += (LD)CV[i][a] * f[i];
+        }
+        for (int type = 2; type <= 3; type++) {
+            LD r, u[3];
+            for (int a = 0; a < 3; a++) u[a] = type == 2 ? (LD)uin[a] : (j[a] + 0.5L * F[a]) / rho;
+            r = type == 2 ? rho : (LD)rho_out;
+            const LD uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+            for (int way = 0; way < 2; way++) {
+                double g[19];
+                for (int i = 0; i < 19; i++) g[i] = f[i];
+                closure_df(g, type, F[0], K, Bc, way == 0);
+                for (int i = 0; i < 19; i++) {
+                    const LD cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+                    const LD feq = weight(i) * r * (1 + 3 * cu + 4.5L * cu * cu - 1.5L * uu);
+                    close_abs = std::fmax(close_abs, (double)(fabsl((LD)g[i] - feq) / weight(i)));
+                }
+            }
+        }
+    }
+    std::printf("closure_abs_over_w %.3e\n", close_abs);
+
     // the form for a force along x (F_y = F_z = 0) against the general form, bit for bit,
     // with a uniform and a per-node F_x, F_x = 0 included
     long xf_mismatch = 0;

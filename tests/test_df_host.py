@@ -11,7 +11,9 @@ kernel compiles (lbm_df.cuh, lbm_collide_df.cuh), against long-double references
   and mass, over random states with |u| up to 0.17, 2 % non-equilibrium, tau 0.51..2;
   some of them with populations below 2^-6, whose moments take the fallback conversion);
 - its form for a force along x (the terms of F_y, F_z left out) against the general form,
-  bit for bit.
+  bit for bit;
+- the equilibrium closures of inlet nodes (f^eq(rho, u_in)) and outlet nodes
+  (f^eq(rho_out, u)) in the same arithmetic.
 """
 import os
 import shutil
@@ -63,6 +65,11 @@ def test_hybrid_collision_matches_long_double(measured):
     assert measured["collide_mass_rel"] <= 5e-14
     # the random states include nodes whose moments take the FP64-pipe conversion
     assert measured["collide_fallback_states"] > 1000
+
+
+def test_equilibrium_closures_match_long_double(measured):
+    # inlet rho * kin_i (two FP64 roundings) and outlet in double-float: ~1e-15 of w_i
+    assert measured["closure_abs_over_w"] <= 1e-13
 
 
 def test_force_along_x_form_equals_the_general_form(measured):
