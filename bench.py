@@ -719,10 +719,10 @@ FP64_FLOPS_PER_NODE = 331
 # ncu capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean of
 # two launches after three warm-up steps), with the hash (step_source_hash) of the library
 # sources they were captured with; the bench reports them only while the sources match.
-TRAFFIC_PER_LAUNCH_256 = {"sources": "386acdbbb575b229",
-                          "f64": 1195588480 + 855821184,
-                          "f32": 686818944 + 416778496,
-                          "f16s": 514765696 + 203579264}
+TRAFFIC_PER_LAUNCH_256 = {"sources": "3a4e394538bd89a2",
+                          "f64": 1194532608 + 855928320,
+                          "f32": 686240768 + 416593920,
+                          "f16s": 515062400 + 203565184}
 
 if __name__ == "__main__":
     main()
