@@ -8,13 +8,15 @@
 //   header(g) cp.async of the group's {first tile, tiles, first node, nodes}, three
 //             groups ahead, into a 4-slot ring;
 //   meta(g)   cp.async of the group's neighbour records (the local tileMap copy of
-//             Algorithm 2, 28 ranks per tile) and per-node words (which directions
-//             bounce, node type, tile and slot) into a 3-slot shared-memory ring;
+//             Algorithm 2: for each of the 27 neighbour positions of a tile, the index of
+//             that tile's first node), the per-node words (which directions bounce, node
+//             type, tile and slot) and source ranks into shared-memory rings;
 //   gather(g) every non-solid node pulls f_i from x - c_i -- its own tile's or a
 //             neighbour tile's data block i -- or, when the word says the source is
 //             solid, dropped or outside the box, its own A_inv(i)(x) (halfway
 //             bounce-back, Sec. 2.2; propagation only between non-solid nodes,
-//             Sec. 3.4): 19 cp.async copies per node into a 2-slot staging ring, so
+//             Sec. 3.4): 19 cp.async copies per node into a staging slot (two for the
+//             4-byte formats; one for FP64, refilled column by column as it is read), so
 //             the bytes in flight do not occupy registers;
 //   compute(g) the moving-wall term of lid links, inlet/outlet closures (equilibrium,
 //             or Zou-He completion then collision), the collision (LBGK + Guo, Eq. 2, 3,
@@ -23,9 +25,9 @@
 // Solid nodes have no storage and issue no copies. A work group is also a storage group:
 // its nodes' values of direction i are one contiguous 256-value data block, so the
 // stores of a group write whole 32-byte sectors (DRAM never reads a sector back to merge
-// a partial write), and a gather reads the source node's padded lane from the neighbour
-// record of its tile (tlane plus the popcount of the tile's non-solid mask below the
-// source slot).
+// a partial write), and a gather reads the source node at the neighbour record of its
+// tile plus the source slot's rank among that tile's non-solid slots (precomputed per
+// node and direction at creation).
 #include <algorithm>
 #include <cmath>
 #include <cstddef>

@@ -73,3 +73,12 @@ def test_reference_arm_line_on_rank_zero():
     assert line["impl"] == "reference" and line["unit"] == "MFLUPS" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["n_gpus"] == 1 and line["higher_is_better"] is True and line["steps"] == 1
+
+
+def test_traffic_figures_are_keyed_to_the_library_code():
+    """The bench reports its stored DRAM traffic only while the library code matches the
+    code it was captured with; comments do not count."""
+    import bench
+    assert bench._code_only("int a; // note\n/* block\n comment */ int b;  \n\n") == "int a;\n int b;"
+    assert len(bench.step_source_hash()) == 16
+    assert set(bench.TRAFFIC_PER_LAUNCH_256) == {"sources", "f64", "f32", "f16s"}
