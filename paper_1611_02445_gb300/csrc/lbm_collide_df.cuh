@@ -191,7 +191,10 @@ LBM_DF_HD void node_moments(const double f[19], int64_t& rho, int64_t& jx, int64
 // XF: K was built with F_y = F_z = 0 (a force along x, or none), so the terms of F_y and
 // F_z, and the force terms of the pairs with c_x = 0, are left out; with those inputs the
 // results equal the general form's bit for bit (the omitted sums add exact zeros).
-template <bool XF>
+// INC: the incompressible equilibrium (Eq. 4, with u from Eq. 6 and the reference density
+// 1 in place of rho): f^eq = w (rho + 3 c.j' + 4.5 (c.j')^2 - 1.5 |j'|^2) and the Guo term
+// with u = j', which is the form above with 1 / rho replaced by 1.
+template <bool XF, bool INC = false>
 LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool uniform_fx) {
     int64_t rho, jx, jy, jz;
     node_moments(f, rho, jx, jy, jz);
@@ -199,7 +202,7 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool unifor
     const dfl Jx = df_from_fix(jx + (uniform_fx ? K.Fx2q : fix_from_double(Fx) >> 1));
     const dfl Jy = df_from_fix(XF ? jy : jy + K.Fy2q);
     const dfl Jz = df_from_fix(XF ? jz : jz + K.Fz2q);
-    const dfl inv = df_recip(df_from_fix(rho));
+    const dfl inv = INC ? df_make(1.0f, 0.0f) : df_recip(df_from_fix(rho));
     const dfl Fxd = uniform_fx ? K.Fx : df_from_double(Fx);
     // P = 1.5 omega |j'|^2 + 3 beta j'.F: the isotropic second-order part of every Y_i
     const dfl JJ = df_add(df_add(df_mul(Jx, Jx), df_mul(Jy, Jy)), df_mul(Jz, Jz));
@@ -216,16 +219,16 @@ LBM_DF_HD void collide_df(double f[19], double Fx, const DFConst& K, bool unifor
 #endif
     // rest population: Y0 = A0 - (w0 / rho) P
     const dfl A0 = df_from_double(K.ow_d[0] * rho_i);
-    const dfl Y0 = df_sub_dom(A0, df_mul(df_mul(K.w0, inv), P));   // |A0| dominates while |u|^2 < 2/3
+    const dfl Y0 = df_sub_dom(A0, df_mul(INC ? K.w0 : df_mul(K.w0, inv), P));   // |A0| dominates while |u|^2 < 2/3
 #if defined(__CUDA_ARCH__)
     f[0] = __fma_rn(K.om1, f[0], df_to_double_pos(Y0));
 #else
     f[0] = std::fma(K.om1, f[0], df_to_double_pos(Y0));
 #endif
     // AP = omega w rho - (w / rho) P of the axis class, halved (exactly) for the diagonal one
-    const dfl AP1 = df_sub_dom(df_from_double(K.ow_d[1] * rho_i), df_mul(df_mul(K.w1, inv), P));
+    const dfl AP1 = df_sub_dom(df_from_double(K.ow_d[1] * rho_i), df_mul(INC ? K.w1 : df_mul(K.w1, inv), P));
     const dfl AP2 = df_scale2(AP1, 0.5f);
-    const dfl r15 = df_mulf(inv, 1.5f);
+    const dfl r15 = INC ? df_make(1.5f, 0.0f) : df_mulf(inv, 1.5f);
     // 3 beta w1 F_x from K with a uniform force; with XF only the pairs with c_x != 0 carry
     // a force
     const dfl G3x = uniform_fx ? K.G3x : df_mul(K.bw3, Fxd);

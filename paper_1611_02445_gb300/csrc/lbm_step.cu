@@ -322,8 +322,16 @@ __device__ __forceinline__ void compute_store(StepSmem<DT>& sm, int mslot, int d
     if constexpr (MODE != STEP_FULL) {
         // calibration kernels: no collision, the gathered values are stored as they are
     } else if constexpr (GEN) {
-        // incompressible equilibrium or MRT
-        collide_model<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
+        // incompressible equilibrium or MRT; for FP64 storage the incompressible LBGK of a
+        // fluid node takes the hybrid collision as well
+        if constexpr (DT == LBM_F64 && !VAR) {
+            if (type == LBM_FLUID && p.coll == LBM_COLL_BGK && p.eq == LBM_EQ_INCOMPR)
+                collide_df<false, true>(v, (double)Fx, p.dfc, !has_gf);
+            else
+                collide_model<R, false>(v, type, p, Fx, Fy, Fz);
+        } else {
+            collide_model<R, Store<DT>::SHIFT>(v, type, p, Fx, Fy, Fz);
+        }
     } else if constexpr (DT == LBM_F64 && !VAR) {
         // FP64 storage: double-float collision for fluid nodes (and Zou-He boundary nodes
         // once completed), and the equilibrium closures of inlet and outlet nodes in the

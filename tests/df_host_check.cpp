@@ -156,6 +156,47 @@ int main() {
     std::printf("collide_mass_rel %.3e\n", mass_rel);
     std::printf("collide_fallback_states %ld\n", fallback_states);
 
+    // the incompressible form (INC): f^eq = w (rho + 3 c.u + 4.5 (c.u)^2 - 1.5 u.u), u = j + F/2,
+    // and the Guo term with that u
+    double inc_abs = 0;
+    for (int n = 0; n < 100000; n++) {
+        const double tau = 0.51 + 1.5 * U(rng), omega = 1.0 / tau, beta = 1.0 - 0.5 / tau;
+        const double F[3] = {1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1), 1e-4 * (2 * U(rng) - 1)};
+        const DFConst K = make_df_const(omega, beta, F[0], F[1], F[2]);
+        double f[19];
+        const double u0[3] = {0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1), 0.1 * (2 * U(rng) - 1)};
+        const double rho0 = 0.95 + 0.1 * U(rng);
+        for (int i = 0; i < 19; i++) {
+            const double cu = CV[i][0] * u0[0] + CV[i][1] * u0[1] + CV[i][2] * u0[2];
+            f[i] = (double)weight(i) * (rho0 + 3 * cu) * (1.0 + 0.02 * (2 * U(rng) - 1));
+        }
+        LD rho = 0, u[3] = {0, 0, 0};
+        for (int i = 0; i < 19; i++) {
+            rho += f[i];
+            for (int a = 0; a < 3; a++) u[a] += (LD)CV[i][a] * f[i];
+        }
+        LD uu = 0, uF = 0;
+        for (int a = 0; a < 3; a++) {
+            u[a] += 0.5L * F[a];
+            uu += u[a] * u[a];
+            uF += u[a] * F[a];
+        }
+        for (int way = 0; way < 2; way++) {
+            double g[19];
+            for (int i = 0; i < 19; i++) g[i] = f[i];
+            collide_df<false, true>(g, F[0], K, way == 0);
+            for (int i = 0; i < 19; i++) {
+                const LD cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+                const LD cF = CV[i][0] * (LD)F[0] + CV[i][1] * (LD)F[1] + CV[i][2] * (LD)F[2];
+                const LD feq = weight(i) * (rho + 3 * cu + 4.5L * cu * cu - 1.5L * uu);
+                const LD S = (LD)beta * weight(i) * (3 * cF - 3 * uF + 9 * cu * cF);
+                const LD ref = (1 - (LD)omega) * f[i] + (LD)omega * feq + S;
+                inc_abs = std::fmax(inc_abs, (double)(fabsl((LD)g[i] - ref) / weight(i)));
+            }
+        }
+    }
+    std::printf("collide_inc_abs_over_w %.3e\n", inc_abs);
+
     // closure_df: inlet f^eq(rho, u_in) and outlet f^eq(rho_out, (j + F/2) / rho) against
     // long double, with a uniform and a per-node F_x
     double close_abs = 0;

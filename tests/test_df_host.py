@@ -13,7 +13,8 @@ kernel compiles (lbm_df.cuh, lbm_collide_df.cuh), against long-double references
 - its form for a force along x (the terms of F_y, F_z left out) against the general form,
   bit for bit;
 - the equilibrium closures of inlet nodes (f^eq(rho, u_in)) and outlet nodes
-  (f^eq(rho_out, u)) in the same arithmetic.
+  (f^eq(rho_out, u)) in the same arithmetic;
+- the collision's form for the incompressible equilibrium (Eq. 4, 6).
 """
 import os
 import shutil
@@ -65,6 +66,10 @@ def test_hybrid_collision_matches_long_double(measured):
     assert measured["collide_mass_rel"] <= 5e-14
     # the random states include nodes whose moments take the FP64-pipe conversion
     assert measured["collide_fallback_states"] > 1000
+
+
+def test_incompressible_form_matches_long_double(measured):
+    assert measured["collide_inc_abs_over_w"] <= 1e-13
 
 
 def test_equilibrium_closures_match_long_double(measured):
