@@ -728,10 +728,10 @@ FP64_FLOPS_PER_NODE = 331
 # ncu capture of this workload (dram__bytes_read.sum + dram__bytes_write.sum, the mean of
 # two launches after three warm-up steps), with the hash (step_source_hash) of the library
 # sources they were captured with; the bench reports them only while the sources match.
-TRAFFIC_PER_LAUNCH_256 = {"sources": "b45cf2245521c067",
-                          "f64": 1195880832 + 855599872,
-                          "f32": 686346368 + 416207744,
-                          "f16s": 514764288 + 203533056}
+TRAFFIC_PER_LAUNCH_256 = {"sources": "2a89652ed962bf29",
+                          "f64": 1194939136 + 855769856,
+                          "f32": 685606912 + 416360448,
+                          "f16s": 511596416 + 203400832}
 
 if __name__ == "__main__":
     main()
