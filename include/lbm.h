@@ -54,15 +54,21 @@ typedef enum {
 } lbm_status;
 
 /* Storage of the populations and the arithmetic of the step.
- *   LBM_F64         FP64 storage. The moment sums and the final (1 - 1/tau) f + Y update
- *                   run in FP64; Y = f^eq/tau + S runs in double-float (pairs of FP32,
- *                   about 46-48 bits), because GB300's FP64 pipe has 2 lanes per SM.
+ *   LBM_F64         FP64 storage. The moments are exact 64-bit fixed-point sums of the
+ *                   stored doubles and the final (1 - 1/tau) f + Y update runs in FP64;
+ *                   Y = f^eq/tau + S runs in double-float (pairs of FP32, about 46-48
+ *                   bits), because GB300's FP64 pipe has 2 lanes per SM. The equilibrium
+ *                   inlet/outlet closures and the incompressible LBGK (lbm_set_model) use
+ *                   the same arithmetic; MRT and the Zou-He completion run in FP64.
  *                   Agrees with FP64 arithmetic to ~1e-14 relative per step.
  *   LBM_F64_NATIVE  FP64 storage, every operation of the step in FP64.
  *   LBM_F32         stores h_i = f_i - w_i as FP32 (the equilibrium-weight shift),
  *                   FP32 arithmetic on h.
  *   LBM_F16S        stores h_i = (f_i - w_i) * 2^12 as IEEE binary16 (round to nearest
- *                   even), FP32 arithmetic on h.
+ *                   even), FP32 arithmetic on h. The step's stores carry each node's
+ *                   rounding residue of mass into direction 0 and of momentum into
+ *                   directions 1-6, so the stored node keeps the computed mass and
+ *                   momentum to within one binary16 spacing.
  *   LBM_F16S_SR     the LBM_F16S format, but the step rounds its stores stochastically:
  *                   each result x (scaled h) is stored as the nearest binary16 to x + d,
  *                   d uniform over one binary16 spacing of x (16-bit dither from a
@@ -74,7 +80,7 @@ typedef enum {
  *                   part of a saved state. lbm_adjoint returns LBM_EUNSUPPORTED for it.
  * lbm_get_f and lbm_get_f_box return f = w_i + h_i in FP64, lbm_set_f rounds f - w_i
  * to the stored format, and lbm_save_state copies the stored values as they are.
- * The equilibrium inlet/outlet closures run in FP64 in both FP64 modes. */
+ * In LBM_F64_NATIVE every closure and model runs in FP64. */
 typedef enum { LBM_F64 = 0, LBM_F32 = 1, LBM_F16S = 2, LBM_F64_NATIVE = 3, LBM_F16S_SR = 4 } lbm_dtype;
 
 enum { LBM_SOLID = 0, LBM_FLUID = 1, LBM_INLET = 2, LBM_OUTLET = 3 };
